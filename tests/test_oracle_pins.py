@@ -1,0 +1,434 @@
+"""Pins of the CPU oracle against values fixed independently of it.
+
+Each test checks one oracle function against something the paper or the
+mathematics fixes: closed forms, analytic demagnetising factors, brute-force
+quadrature computed here with numpy's Gauss-Legendre rule, invariances, and
+exhaustive checks on tiny meshes.  None of these needs a GPU.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "analytic_values.json")))
+
+
+# ---------------------------------------------------------------- quadrature
+def _duffy_rule(q):
+    g, w = np.polynomial.legendre.leggauss(q)
+    g = 0.5 * (g + 1.0)
+    w = 0.5 * w
+    U, Vv = np.meshgrid(g, g, indexing="ij")
+    WU, WV = np.meshgrid(w, w, indexing="ij")
+    s = U.ravel()
+    t = (Vv * (1.0 - U)).ravel()
+    wt = (WU * WV * (1.0 - U)).ravel()
+    return s, t, wt
+
+
+def brute_corner_weights(x, r0, r1, r2, nsub=24, q=12):
+    """(1/4pi) int_T phi_a n.(x-y)/|x-y|^3 dS by subdivided product Gauss quadrature."""
+    r0, r1, r2, x = (np.asarray(v, dtype=np.float64) for v in (r0, r1, r2, x))
+    n = np.cross(r1 - r0, r2 - r0)
+    twoA = np.linalg.norm(n)
+    n /= twoA
+    s, t, wt = _duffy_rule(q)
+    out = np.zeros(3)
+    h = 1.0 / nsub
+    # sub-triangles of the reference triangle: "up" and "down" cells
+    for i in range(nsub):
+        for j in range(nsub - i):
+            cells = [((i * h, j * h), (h, 0.0), (0.0, h))]
+            if i + j < nsub - 1:
+                cells.append((((i + 1) * h, (j + 1) * h), (-h, 0.0), (0.0, -h)))
+            for (a0, b0), (da1, db1), (da2, db2) in cells:
+                S = a0 + s * da1 + t * da2
+                T = b0 + s * db1 + t * db2
+                y = r0[None, :] + S[:, None] * (r1 - r0)[None, :] + T[:, None] * (r2 - r0)[None, :]
+                d = x[None, :] - y
+                R3 = np.linalg.norm(d, axis=1) ** 3
+                f = (d @ n) / R3 / (4.0 * math.pi)
+                jac = twoA * h * h  # sub-cell area ratio h^2
+                phi = np.stack([1.0 - S - T, S, T])
+                out += (phi * (f * wt * jac)[None, :]).sum(axis=1)
+    return out
+
+
+def _rand_tri(g):
+    r = g.standard_normal((3, 3))
+    return r[0], r[1], r[2]
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_lindholm_matches_brute_force_quadrature(case):
+    g = np.random.default_rng(100 + case)
+    r0, r1, r2 = _rand_tri(g)
+    c = (r0 + r1 + r2) / 3.0
+    n = np.cross(r1 - r0, r2 - r0)
+    n /= np.linalg.norm(n)
+    size = max(np.linalg.norm(r1 - r0), np.linalg.norm(r2 - r1), np.linalg.norm(r0 - r2))
+    # far, moderate, and close (above the interior, below, beside an edge)
+    offs = [3.0, 1.0, 0.3, -0.3, 0.15]
+    o = offs[case % len(offs)]
+    lateral = g.standard_normal(3)
+    lateral -= (lateral @ n) * n
+    x = c + o * size * n + (0.2 * size if case >= 5 else 0.0) * lateral / np.linalg.norm(lateral)
+    L = oracle.lindholm(x, r0, r1, r2)
+    B = brute_corner_weights(x, r0, r1, r2)
+    assert np.linalg.norm(L - B) <= 1e-9 * max(np.linalg.norm(B), 1e-300), (L, B)
+
+
+def test_lindholm_corner_sum_is_solid_angle():
+    g = np.random.default_rng(7)
+    for _ in range(50):
+        r0, r1, r2 = _rand_tri(g)
+        x = g.standard_normal(3) * 2.0
+        L = oracle.lindholm(x, r0, r1, r2)
+        om = oracle.solid_angle(x, r0, r1, r2)
+        assert abs(L.sum() + om / (4 * math.pi)) < 1e-13
+
+
+def test_lindholm_coplanar_and_vertex_are_zero():
+    r0, r1, r2 = np.array([0.0, 0, 0]), np.array([1.0, 0, 0]), np.array([0.0, 1, 0])
+    assert np.all(oracle.lindholm(np.array([2.0, 3.0, 0.0]), r0, r1, r2) == 0.0)
+    assert np.all(oracle.lindholm(r1, r0, r1, r2) == 0.0)
+
+
+def test_solid_angle_closed_forms():
+    # a cube face seen from the cube centre subtends 4 pi / 6; the two
+    # triangles of a face split it into halves by symmetry.
+    c = np.zeros(3)
+    a, b, cc, d = (np.array(p, dtype=float) for p in ([1, -1, 1], [1, 1, 1], [-1, 1, 1], [-1, -1, 1]))
+    # outward normal +z: seen from the centre the surface points away -> positive
+    om = oracle.solid_angle(c, a, b, cc) + oracle.solid_angle(c, a, cc, d)
+    assert abs(om - GOLDEN["cube_face_from_centre"]["value"]) < 1e-14
+    # point on the axis of a unit right-isoceles... use the regular-tetrahedron
+    # face from the centroid: 4 pi / 4
+    t = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], dtype=float)
+    faces = [(0, 1, 2), (0, 3, 1), (0, 2, 3), (1, 3, 2)]
+    tot = 0.0
+    for f in faces:
+        om = oracle.solid_angle(c, t[f[0]], t[f[1]], t[f[2]])
+        assert abs(abs(om) - math.pi) < 1e-14
+        tot += om
+    assert abs(abs(tot) - 4 * math.pi) < 1e-13
+
+
+def test_solid_angle_matches_quadrature():
+    g = np.random.default_rng(3)
+    for _ in range(5):
+        r0, r1, r2 = _rand_tri(g)
+        x = g.standard_normal(3) * 1.5
+        # Omega = -4 pi * sum of corner weights of the brute-force integral
+        B = brute_corner_weights(x, r0, r1, r2, nsub=16, q=10)
+        assert abs(oracle.solid_angle(x, r0, r1, r2) + 4 * math.pi * B.sum()) < 1e-8
+
+
+def test_psi_cube_corner_edge_face():
+    m = synth.cube_surface(4)
+    ps = oracle.psi(m.xyz, m.tri)
+    onb = np.isclose(m.xyz, 0.0) | np.isclose(m.xyz, 1.0)
+    nb = onb.sum(axis=1)  # number of bounding planes through the node
+    assert np.allclose(ps[nb == 3], GOLDEN["cube_corner_solid_angle"]["value"], atol=1e-12)
+    assert np.allclose(ps[nb == 2], GOLDEN["cube_edge_solid_angle"]["value"], atol=1e-12)
+    assert np.allclose(ps[nb == 1], GOLDEN["cube_face_solid_angle"]["value"], atol=1e-12)
+
+
+@pytest.mark.parametrize("mk", [lambda: synth.icosphere(3), lambda: synth.cube_surface(6),
+                                lambda: synth.ellipsoid(2), lambda: synth.box_surface(3, 5, 2, 1.0, 2.0, 0.3)])
+def test_gauss_identity_constant_vector(mk):
+    m = mk()
+    M = oracle.dense_matrix(m.xyz, m.tri)
+    val = GOLDEN["constant_u1_response"]["value"]
+    assert np.max(np.abs(M.sum(axis=1) - val)) < 1e-12
+
+
+def test_dense_rows_and_matvec_agree_with_matrix():
+    m = synth.icosphere(2)
+    M = oracle.dense_matrix(m.xyz, m.tri)
+    rows = np.array([0, 7, 100, 161])
+    assert np.array_equal(oracle.dense_rows(m.xyz, m.tri, rows), M[rows])
+    x = synth.gaussian_rhs(m.n_vertices, 3, 5)
+    assert np.allclose(oracle.dense_matvec(m.xyz, m.tri, x), (M @ x.T).T, rtol=1e-13, atol=1e-13)
+
+
+def test_sphere_dipole_eigenvalue_converges():
+    lam = GOLDEN["sphere_dipole_eigenvalue"]["value"]
+    errs = []
+    for lvl in (1, 2, 3):
+        m = synth.icosphere(lvl)
+        z = m.xyz[:, 2]
+        y = oracle.dense_matvec(m.xyz, m.tri, z[None, :])[0]
+        errs.append(np.linalg.norm(y - lam * z) / np.linalg.norm(lam * z))
+    # O(h^2): each refinement halves h
+    assert errs[1] < errs[0] / 3.0 and errs[2] < errs[1] / 3.0
+    assert errs[2] < 3e-3
+
+
+def test_sphere_demag_factor_converges_to_one_third():
+    target = GOLDEN["sphere_demag_factor"]["value"]
+    errs = []
+    for lvl in (2, 3, 4):
+        m = synth.icosphere(lvl)
+        u1 = m.xyz[:, 2]
+        u2 = oracle.dense_matvec(m.xyz, m.tri, u1[None, :])[0]
+        errs.append(abs(oracle.demag_factor(m.xyz, m.tri, u1 + u2) - target))
+    assert errs[1] < errs[0] and errs[2] < errs[1]
+    assert errs[2] < 1e-3
+
+
+def test_cube_demag_factor_symmetry_and_convergence():
+    target = GOLDEN["cube_demag_factor"]["value"]
+    errs = []
+    for n in (4, 8, 12):
+        m = synth.cube_surface(n)
+        M = oracle.dense_matrix(m.xyz, m.tri)
+        Ns = []
+        for d in range(3):
+            e = np.zeros(3)
+            e[d] = 1.0
+            u1 = m.xyz @ e
+            Ns.append(oracle.demag_factor(m.xyz, m.tri, u1 + M @ u1, e))
+        # the structured split breaks the cube symmetry only at rounding level here
+        assert max(Ns) - min(Ns) < 1e-12
+        errs.append(abs(Ns[0] - target))
+    # the edge singularity of the field slows convergence, but it is monotone
+    assert errs[1] < errs[0] and errs[2] < errs[1] and errs[2] < 5e-3, errs
+
+
+def test_rigid_motion_and_scale_invariance():
+    m = synth.icosphere(2)
+    M = oracle.dense_matrix(m.xyz, m.tri)
+    th = 0.7
+    R = np.array([[math.cos(th), -math.sin(th), 0], [math.sin(th), math.cos(th), 0], [0, 0, 1.0]])
+    R = R @ np.array([[1, 0, 0], [0, math.cos(0.3), -math.sin(0.3)], [0, math.sin(0.3), math.cos(0.3)]])
+    m2 = synth.transformed(m, R, [3.0, -1.0, 2.0], 17.0)
+    M2 = oracle.dense_matrix(m2.xyz, m2.tri)
+    assert np.max(np.abs(M - M2)) < 1e-12
+
+
+# ---------------------------------------------------------------- H2 pieces
+def test_gauss_legendre_matches_numpy():
+    for q in (1, 2, 4, 7, 12):
+        x, w = oracle.gauss_legendre01(q)
+        g, gw = np.polynomial.legendre.leggauss(q)
+        order = np.argsort(0.5 * (g + 1))
+        assert np.allclose(np.sort(x), 0.5 * (g[order] + 1), atol=1e-15)
+        assert np.allclose(w[np.argsort(x)], 0.5 * gw[order], atol=1e-15)
+        for p in range(2 * q):
+            assert abs(np.sum(w * x ** p) - 1.0 / (p + 1)) < 1e-14
+
+
+def test_chebyshev_points_closed_form():
+    box = np.array([-1.0, 0.5, 2.0, 3.0, 1.5, 2.25])
+    m = 4
+    P = oracle.cheb_points(box, m)
+    for a in range(m):
+        for b in range(m):
+            for c in range(m):
+                nu = (a * m + b) * m + c
+                want = [box[d] + 0.5 * (box[3 + d] - box[d]) * (1 + math.cos((2 * i + 1) * math.pi / (2 * m)))
+                        for d, i in zip(range(3), (a, b, c))]
+                assert np.allclose(P[nu], want, atol=1e-15)
+
+
+def test_lagrange_reproduces_polynomials_and_gradients():
+    g = np.random.default_rng(11)
+    box = np.array([0.1, -0.4, 0.0, 0.9, 0.2, 0.3])
+    for m in (2, 3, 5):
+        P = oracle.cheb_points(box, m)
+        coef = g.standard_normal((m, m, m))
+
+        def poly(x):
+            return sum(coef[i, j, k] * x[0] ** i * x[1] ** j * x[2] ** k
+                       for i in range(m) for j in range(m) for k in range(m))
+
+        def dpoly(x):
+            gx = sum(coef[i, j, k] * i * x[0] ** max(i - 1, 0) * x[1] ** j * x[2] ** k
+                     for i in range(m) for j in range(m) for k in range(m))
+            gy = sum(coef[i, j, k] * j * x[0] ** i * x[1] ** max(j - 1, 0) * x[2] ** k
+                     for i in range(m) for j in range(m) for k in range(m))
+            gz = sum(coef[i, j, k] * k * x[0] ** i * x[1] ** j * x[2] ** max(k - 1, 0)
+                     for i in range(m) for j in range(m) for k in range(m))
+            return np.array([gx, gy, gz])
+
+        vals = np.array([poly(p) for p in P])
+        for _ in range(5):
+            x = box[:3] + g.uniform(-0.1, 1.1, 3) * (box[3:] - box[:3])
+            Lv, Lg = oracle.lagrange3(box, m, x)
+            scale = np.abs(Lv).sum()
+            assert abs(Lv.sum() - 1.0) < 1e-14 * scale * m ** 3
+            assert abs(Lv @ vals - poly(x)) < 1e-12 * scale * np.abs(vals).max()
+            assert np.allclose(Lg.T @ vals, dpoly(x), rtol=1e-9, atol=1e-9)
+
+
+def _tri_geom(m):
+    n, A = oracle.triangle_normals_areas(m.xyz, m.tri)
+    return n, A
+
+
+def test_W_integrates_linear_polynomials_exactly():
+    """sum_mu W(j,mu) p(y_mu) = sum_{T contains j} (a.n_T) A_T / 3 for p(y) = a.y + b."""
+    m = synth.icosphere(2)
+    h = oracle.H2Oracle(m.xyz, m.tri, 3, 16, 2.0)
+    tr = h.tree()
+    n, A = _tri_geom(m)
+    a = np.array([0.3, -1.2, 0.7])
+    for c in (0, 1, 5, h.n_clusters - 1):
+        sz = tr["size"][c]
+        V, W = h.cluster_bases(c, sz)
+        P = oracle.cheb_points(tr["box"][c], 3)
+        pv = P @ a + 0.25
+        nodes = tr["perm"][tr["start"][c]:tr["start"][c] + sz]
+        for row, j in enumerate(nodes):
+            tris = np.where((m.tri == j).any(axis=1))[0]
+            want = np.sum((n[tris] @ a) * A[tris]) / 3.0
+            assert abs(W[row] @ pv - want) < 1e-12
+        # V: interpolation of the linear function at the nodes is exact
+        assert np.allclose(V @ pv, m.xyz[nodes] @ a + 0.25, atol=1e-12)
+
+
+def test_W_quadrature_order_is_exact():
+    m = synth.icosphere(2)
+    for mm in (3, 4):
+        h1 = oracle.H2Oracle(m.xyz, m.tri, mm, 16, 2.0)
+        h2 = oracle.H2Oracle(m.xyz, m.tri, mm, 16, 2.0, q=h1.q + 3)
+        tr = h1.tree()
+        for c in (1, 3, 7):
+            _, W1 = h1.cluster_bases(c, tr["size"][c])
+            _, W2 = h2.cluster_bases(c, tr["size"][c])
+            assert np.max(np.abs(W1 - W2)) <= 1e-12 * np.max(np.abs(W1))
+
+
+def test_tree_invariants():
+    for mk, leaf in ((lambda: synth.icosphere(3), 32), (lambda: synth.cube_surface(10), 20)):
+        m = mk()
+        h = oracle.H2Oracle(m.xyz, m.tri, 3, leaf, 2.0, store=False)
+        t = h.tree()
+        assert np.array_equal(np.sort(t["perm"]), np.arange(m.n_vertices))
+        for c in range(h.n_clusters):
+            st, sz = t["start"][c], t["size"][c]
+            nodes = t["perm"][st:st + sz]
+            c0, c1 = t["child0"][c], t["child1"][c]
+            if c0 < 0:
+                assert sz <= leaf
+            else:
+                assert sz > leaf
+                assert t["start"][c0] == st and t["start"][c1] == st + t["size"][c0]
+                assert t["size"][c0] + t["size"][c1] == sz
+                assert t["level"][c0] == t["level"][c] + 1 and t["parent"][c0] == c
+                p = m.xyz[nodes]
+                lo, hi = p.min(axis=0), p.max(axis=0)
+                ax = int(np.argmax(hi - lo))
+                mid = (lo[ax] + hi[ax]) / 2.0
+                left = t["perm"][st:st + t["size"][c0]]
+                right = t["perm"][st + t["size"][c0]:st + sz]
+                assert np.all(m.xyz[left, ax] <= mid) and np.all(m.xyz[right, ax] > mid)
+                # stable: relative order kept
+                pos = {v: i for i, v in enumerate(nodes)}
+                assert all(pos[a] < pos[b] for a, b in zip(left[:-1], left[1:]))
+            # box contains the support (all triangles at its nodes)
+            tris = np.where(np.isin(m.tri, nodes).any(axis=1))[0]
+            pts = m.xyz[m.tri[tris]].reshape(-1, 3)
+            assert np.all(pts >= t["box"][c][:3] - 1e-15) and np.all(pts <= t["box"][c][3:] + 1e-15)
+            w = t["box"][c][3:] - t["box"][c][:3]
+            assert np.all(w >= 0.25 * w.max() * (1 - 1e-12))
+        # level numbering is breadth-first
+        assert np.all(np.diff(t["level"]) >= 0)
+
+
+def test_block_partition_covers_every_pair_once():
+    m = synth.icosphere(2)
+    h = oracle.H2Oracle(m.xyz, m.tri, 3, 8, 2.0, store=False)
+    t = h.tree()
+    b = h.blocks()
+    cover = np.zeros((m.n_vertices, m.n_vertices), dtype=np.int32)
+    for kind in ("far", "near"):
+        for tt, ss in zip(b[kind + "_t"], b[kind + "_s"]):
+            ti = t["perm"][t["start"][tt]:t["start"][tt] + t["size"][tt]]
+            si = t["perm"][t["start"][ss]:t["start"][ss] + t["size"][ss]]
+            cover[np.ix_(ti, si)] += 1
+            adm = oracle.admissible(t["box"][tt], t["box"][ss], 2.0)
+            if kind == "far":
+                assert adm
+            else:
+                assert not adm and t["child0"][tt] < 0 and t["child0"][ss] < 0
+    assert np.all(cover == 1)
+    assert h.n_far > 0
+
+
+def test_nested_bases_follow_from_direct_ones():
+    """V_parent|child = V_child E and W_parent|child = W_child E, E(nu',nu) = L^parent_nu(x^child_nu')."""
+    m = synth.icosphere(3)
+    mm = 3
+    h = oracle.H2Oracle(m.xyz, m.tri, mm, 32, 2.0, store=False)
+    t = h.tree()
+    for c in range(h.n_clusters):
+        c0 = t["child0"][c]
+        if c0 < 0:
+            continue
+        Vp, Wp = h.cluster_bases(c, t["size"][c])
+        for ch in (c0, t["child1"][c]):
+            Vc, Wc = h.cluster_bases(ch, t["size"][ch])
+            Pc = oracle.cheb_points(t["box"][ch], mm)
+            E = np.array([oracle.lagrange3(t["box"][c], mm, p)[0] for p in Pc])
+            off = t["start"][ch] - t["start"][c]
+            rows = slice(off, off + t["size"][ch])
+            assert np.max(np.abs(Vp[rows] - Vc @ E)) <= 1e-11 * max(1.0, np.max(np.abs(Vp)))
+            assert np.max(np.abs(Wp[rows] - Wc @ E)) <= 1e-11 * max(1.0, np.max(np.abs(Wp)))
+        if c > 6:
+            break
+
+
+def test_h2_converges_to_dense_in_m():
+    m = synth.icosphere(3)
+    M = oracle.dense_matrix(m.xyz, m.tri)
+    x = synth.gaussian_rhs(m.n_vertices, 2, 9)
+    y = (M @ x.T).T
+    errs = []
+    for mm in (2, 3, 4, 5):
+        h = oracle.H2Oracle(m.xyz, m.tri, mm, 32, 2.0)
+        errs.append(np.linalg.norm(h.matvec(x) - y) / np.linalg.norm(y))
+    for a, b in zip(errs[:-1], errs[1:]):
+        assert b < a / 2.5, errs
+    assert errs[-1] < 1e-4
+
+
+def test_h2_is_exact_without_far_blocks_and_rows_match():
+    m = synth.icosphere(2)
+    M = oracle.dense_matrix(m.xyz, m.tri)
+    x = synth.gaussian_rhs(m.n_vertices, 1, 1)
+    # eta tiny -> nothing admissible -> all near -> exact
+    h = oracle.H2Oracle(m.xyz, m.tri, 3, 16, 1e-6)
+    assert h.n_far == 0
+    assert np.allclose(h.matvec(x)[0], M @ x[0], rtol=0, atol=1e-13)
+    h2 = oracle.H2Oracle(m.xyz, m.tri, 3, 16, 2.0)
+    rows = np.array([0, 3, 50, 161])
+    assert np.allclose(h2.rows(x, rows), h2.matvec(x)[:, rows], atol=1e-14)
+
+
+def test_h2_far_block_equals_explicit_product():
+    m = synth.icosphere(3)
+    Mfull = oracle.dense_matrix(m.xyz, m.tri)
+    errs = []
+    for mm in (3, 5):
+        h = oracle.H2Oracle(m.xyz, m.tri, mm, 32, 2.0)
+        t, b = h.tree(), h.blocks()
+        tt, ss = b["far_t"][0], b["far_s"][0]
+        V, _ = h.cluster_bases(tt, t["size"][tt])
+        _, W = h.cluster_bases(ss, t["size"][ss])
+        S = h.coupling(tt, ss)
+        Pt = oracle.cheb_points(t["box"][tt], mm)
+        Ps = oracle.cheb_points(t["box"][ss], mm)
+        d = np.linalg.norm(Pt[:, None, :] - Ps[None, :, :], axis=2)
+        assert np.allclose(S, 1.0 / (4 * math.pi * d), rtol=1e-15, atol=0)
+        ti = t["perm"][t["start"][tt]:t["start"][tt] + t["size"][tt]]
+        si = t["perm"][t["start"][ss]:t["start"][ss] + t["size"][ss]]
+        Mblk = Mfull[np.ix_(ti, si)]
+        errs.append(np.linalg.norm(V @ S @ W.T - Mblk) / np.linalg.norm(Mblk))
+    assert errs[0] < 2e-2 and errs[1] < errs[0] / 5.0, errs
