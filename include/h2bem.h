@@ -1,0 +1,177 @@
+/*
+ * h2bem: boundary double-layer operator of the Fredkin-Koehler FEM/BEM method
+ * with H2-matrix compression, on one NVIDIA GB300 (sm_103a).
+ *
+ * Computes u2|Gamma = M u1|Gamma (arXiv:1811.05731, Eq. (denseMat)) with
+ *   M = K + D,
+ *   K_ij = (1/4pi) oint phi_j(y) n_y.(xi_i - y)/|xi_i - y|^3 dS_y
+ *          (collocation at the nodes xi_i, linear nodal basis phi_j on a flat
+ *          triangle mesh, Eq. (matrix_definition); entries by Lindholm's
+ *          closed form),
+ *   D_ii = Psi(xi_i)/(4 pi) - 1, Psi the interior solid angle (Eq. (mainInt)),
+ * where K is compressed as an H2 matrix (Section "H2-Matrix Compression"):
+ * a geometric cluster tree, eta-admissible blocks K|t x s ~ V_t S_ts W_s^T
+ * with tensor Chebyshev interpolation of order m (k = m^3 coefficients per
+ * cluster), nested bases through transfer matrices E_t, and exact FP64 near
+ * blocks.  The sign convention of the double-layer term is the one under
+ * which a constant u1 gives u2 = -u1 (M 1 = -1).
+ *
+ * Conventions for every entry point:
+ *  - Return value: H2_OK (0) or a negative h2_status; no exception crosses
+ *    this interface.  h2_error_string() names a code.
+ *  - Streams: `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ *    Work is stream-ordered; h2_matvec returns before the GPU finishes when
+ *    given device buffers.
+ *  - Ownership: handles are created by the library and released with
+ *    h2_free.  Mesh arrays are copied.  Vector buffers stay owned by the
+ *    caller.  An operator keeps its geometry alive until both are freed.
+ *  - Thread safety: calls on one handle must not overlap (one workspace per
+ *    operator).
+ */
+#ifndef H2BEM_H
+#define H2BEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct h2_handle h2_handle;   /* opaque: a geometry or an operator */
+
+typedef enum {
+    H2_OK = 0,
+    H2_ERR_INVALID_ARG = -1,          /* null pointer, size out of range, bad parameter */
+    H2_ERR_MESH_OPEN = -2,            /* an edge is not shared by exactly two triangles */
+    H2_ERR_MESH_ORIENTATION = -3,     /* inconsistent orientation or enclosed volume <= 0 */
+    H2_ERR_DEGENERATE_TRIANGLE = -4,  /* zero-area triangle or repeated corner */
+    H2_ERR_OOM = -5,                  /* device or host allocation failed */
+    H2_ERR_CUDA = -6,                 /* a CUDA runtime call failed */
+    H2_ERR_TIMEOUT = -7,              /* a bounded device-side wait gave up */
+    H2_ERR_RHS_EXCEEDS_MAX = -8,      /* r > h2_params.max_rhs */
+    H2_ERR_WRONG_HANDLE = -9          /* geometry given where an operator is needed, or vice versa */
+} h2_status;
+
+/* Storage/arithmetic precision of the far field (transfer, coupling and leaf
+ * bases).  Near blocks, the solid-angle diagonal, the geometry and the final
+ * per-node sum are FP64 in every mode.
+ *  H2_FP64: everything FP64.
+ *  H2_FP32: far-field matrices stored in FP32, FP32 products with FP32
+ *           accumulation per block, block sums added in FP64. */
+typedef enum { H2_FP64 = 0, H2_FP32 = 1 } h2_precision;
+
+typedef struct {
+    int32_t m;              /* Chebyshev points per axis, 1..5 (k = m^3 <= 125)       */
+    int32_t leaf;           /* maximum nodes per leaf cluster, 1..128                 */
+    double eta;             /* admissibility: max(diam) <= eta * dist                 */
+    double box_inflation;   /* rho: every box side >= rho * longest side (0.25)       */
+    int32_t precision;      /* h2_precision                                           */
+    int32_t max_rhs;        /* largest r accepted by h2_matvec (workspace size), >= 1 */
+    int32_t reserved[4];    /* must be zero                                           */
+} h2_params;
+
+/* Fills `p` with the defaults: m = 4, leaf = 64, eta = 2, rho = 0.25, FP64, max_rhs = 1. */
+void h2_default_params(h2_params* p);
+
+/* Build a geometry handle from a closed, outward-oriented triangle mesh
+ * (Section "Discretization": nodes xi_i, piecewise linear nodal basis).
+ *   xyz: host, n_vertices x 3 doubles, row-major.
+ *   tri: host, n_triangles x 3 int32 node indices (0-based), counter-clockwise
+ *        seen from outside.
+ * Validates closedness, orientation and non-degeneracy (error codes above),
+ * copies the mesh to the device and computes the interior solid angle Psi at
+ * every node (Eq. (mainInt)).  Returns the handle in *out_geom. */
+int h2_build_geometry(const double* xyz, int64_t n_vertices, const int32_t* tri,
+                      int64_t n_triangles, void* cuda_stream, h2_handle** out_geom);
+
+/* Assemble the H2 operator on the device (Section "H2-Matrix Compression"):
+ * cluster tree, block partition, leaf bases V_t and W_t, transfer matrices
+ * E_t, coupling matrices S_ts and FP64 Lindholm near blocks with the
+ * solid-angle diagonal.  `p` may be NULL (defaults).  Synchronous. */
+int h2_assemble(const h2_handle* geom, const h2_params* p, h2_handle** out_op);
+
+/* u2 = M u1 for r right-hand sides (Eq. (denseMat)).
+ *   u1, u2: r x N doubles, row-major (right-hand side c at offset c*N), node
+ *           order of the input mesh.  Either both device pointers or both
+ *           host pointers; with host pointers the call copies in and out on
+ *           `cuda_stream` and returns after the result is in u2.
+ *   1 <= r <= max_rhs.  u1 and u2 must not overlap.  u2 is overwritten. */
+int h2_matvec(h2_handle* op, const double* u1, double* u2, int32_t r, void* cuda_stream);
+
+/* Counts and sizes of an operator (Section "Results", "Data compression":
+ * storage of the compressed operator and the compression ratio
+ * r = 1 - size(compressed) / size(dense)). */
+typedef struct {
+    int64_t n_vertices, n_triangles;
+    int32_t n_clusters, n_levels, n_leaves, k;
+    int64_t n_far_blocks, n_near_blocks;
+    int64_t near_entries;          /* FP64 near-field entries (incl. the diagonal)      */
+    int64_t far_coefficients;      /* coupling entries: n_far_blocks * k^2              */
+    int64_t basis_coefficients;    /* stored V, W and transfer entries                  */
+    int64_t bytes_far;             /* device bytes of S, V, W and the transfers         */
+    int64_t bytes_near;            /* device bytes of the near blocks                   */
+    int64_t bytes_streamed;        /* matrix bytes one matvec reads (each exactly once) */
+    int64_t macs_per_rhs;          /* multiply-adds of one matvec per right-hand side   */
+    double compression_ratio;      /* 1 - (far + near bytes) / (8 N^2)                  */
+    double assemble_seconds;
+    int32_t precision, max_rhs;
+    int32_t n_launches_matvec;     /* kernel launches per h2_matvec                     */
+    int32_t n_passes;              /* block-sparse passes per h2_matvec                 */
+} h2_stats_t;
+
+int h2_stats(const h2_handle* op, h2_stats_t* out);
+
+/* Copy the cluster tree out (host arrays; sizes from h2_stats):
+ *   perm[N]: node at tree position q; start/size/parent/child0/child1/level
+ *   [n_clusters] (child = -1 at leaves; clusters numbered level by level);
+ *   box[6*n_clusters]: lo xyz, hi xyz of the interpolation box. */
+int h2_get_tree(const h2_handle* op, int32_t* perm, int32_t* start, int32_t* size,
+                int32_t* parent, int32_t* child0, int32_t* child1, int32_t* level,
+                double* box);
+
+/* Copy the block partition out (host arrays of n_far_blocks / n_near_blocks). */
+int h2_get_blocks(const h2_handle* op, int32_t* far_t, int32_t* far_s, int32_t* near_t,
+                  int32_t* near_s);
+
+/* Copy Psi (N doubles, mesh node order) of a geometry or operator to host memory. */
+int h2_get_psi(const h2_handle* h, double* psi);
+
+/* Synchronises the device and reports whether any h2_matvec on `op` since
+ * the last call gave up a bounded device-side wait (H2_ERR_TIMEOUT; the
+ * result of that product is then undefined).  Clears the flag. */
+int h2_device_status(h2_handle* op);
+
+/* Per-pass timing (a measurement aid, not needed for computing).  While
+ * enabled, every h2_matvec on `op` records CUDA events on its stream before
+ * and after each kernel launch.  Enabling or disabling drops what was
+ * recorded so far. */
+int h2_profile_enable(h2_handle* op, int32_t enable);
+
+/* Synchronises on the recorded events and returns, per launch of one
+ * h2_matvec in launch order (entry 0 = the input gather, then one entry per
+ * pass), the pass kind (0 gather, 1 upward leaf projection, 2 upward
+ * transfer, 3 coupling, 4 downward transfer, 5 leaf expansion + near field),
+ * the total milliseconds over all recorded calls, the matrix bytes and the
+ * multiply-adds (per right-hand side) of one launch, and its grid size.
+ * Arrays hold `capacity` entries (any may be NULL); *n_entries is the number
+ * of launches per call and *n_calls the number of recorded calls.  Clears the
+ * recorded events. */
+int h2_profile_read(h2_handle* op, int32_t capacity, int32_t* kind, double* ms_total,
+                    int64_t* bytes, int64_t* macs, int32_t* grid, int32_t* n_calls,
+                    int32_t* n_entries);
+
+/* Release a geometry or operator handle; NULL is a no-op.  Releasing a handle
+ * twice is undefined. */
+int h2_free(h2_handle* h);
+
+/* Static string naming a status code. */
+const char* h2_error_string(int code);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char* h2_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* H2BEM_H */

@@ -1,0 +1,24 @@
+"""h2bem on GB300: the boundary double-layer operator of the Fredkin-Koehler
+FEM/BEM method as an H2 matrix (arXiv:1811.05731), assembled and applied by
+hand-written CUDA kernels for sm_103a.
+
+The compute path is the C-ABI library ``libh2bem`` (``include/h2bem.h``); this
+package only marshals arguments to it.  The functions carry the C names:
+
+* :func:`h2_build_geometry` - closed surface mesh -> geometry handle
+  (mesh checks, solid angle Psi at every node; Eq. mainInt)
+* :func:`h2_assemble`       - geometry + parameters -> H2 operator
+  (Section "H2-Matrix Compression")
+* :func:`h2_matvec`         - u2 = M u1 for r right-hand sides (Eq. denseMat)
+* :func:`h2_free`           - release a handle
+
+:class:`Geometry` and :class:`Operator` wrap the handles.  There is no CPU
+fallback: if the library is missing or cannot be loaded, every call raises.
+"""
+from ._lib import (  # noqa: F401
+    H2Error, Params, Stats, FP64, FP32, lib, load,
+    h2_default_params, h2_build_geometry, h2_assemble, h2_matvec, h2_free, h2_stats,
+    h2_get_tree, h2_get_blocks, h2_get_psi, h2_device_status, h2_error_string,
+    Geometry, Operator,
+)
+from .build import build, lib_path  # noqa: F401

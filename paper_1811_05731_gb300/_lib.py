@@ -1,0 +1,267 @@
+"""ctypes binding of libh2bem (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .build import lib_path
+
+FP64 = 0
+FP32 = 1
+
+_LIB = None
+_LOCK = threading.Lock()
+_c_d = ctypes.POINTER(ctypes.c_double)
+_c_i32 = ctypes.POINTER(ctypes.c_int32)
+_vp = ctypes.c_void_p
+
+
+class H2Error(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = f"{where}: {h2_error_string(code)} ({code})"
+        try:
+            extra = lib().h2_last_error_message().decode()
+            if extra:
+                msg += f": {extra}"
+        except Exception:
+            pass
+        super().__init__(msg)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("leaf", ctypes.c_int32), ("eta", ctypes.c_double),
+                ("box_inflation", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("max_rhs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
+                ("n_clusters", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("n_leaves", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("n_far_blocks", ctypes.c_int64), ("n_near_blocks", ctypes.c_int64),
+                ("near_entries", ctypes.c_int64), ("far_coefficients", ctypes.c_int64),
+                ("basis_coefficients", ctypes.c_int64), ("bytes_far", ctypes.c_int64),
+                ("bytes_near", ctypes.c_int64), ("bytes_streamed", ctypes.c_int64),
+                ("macs_per_rhs", ctypes.c_int64), ("compression_ratio", ctypes.c_double),
+                ("assemble_seconds", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("max_rhs", ctypes.c_int32), ("n_launches_matvec", ctypes.c_int32),
+                ("n_passes", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def load(path: str | None = None):
+    """Load libh2bem (built by :func:`paper_1811_05731_gb300.build`); raises if absent."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        p = path or lib_path()
+        if not os.path.exists(p):
+            raise RuntimeError(f"libh2bem is not built ({p}); run paper_1811_05731_gb300.build()")
+        L = ctypes.CDLL(p)
+        L.h2_default_params.argtypes = [ctypes.POINTER(Params)]
+        L.h2_default_params.restype = None
+        L.h2_error_string.argtypes = [ctypes.c_int]
+        L.h2_error_string.restype = ctypes.c_char_p
+        L.h2_last_error_message.argtypes = []
+        L.h2_last_error_message.restype = ctypes.c_char_p
+        L.h2_build_geometry.argtypes = [_c_d, ctypes.c_int64, _c_i32, ctypes.c_int64, _vp,
+                                        ctypes.POINTER(_vp)]
+        L.h2_assemble.argtypes = [_vp, ctypes.POINTER(Params), ctypes.POINTER(_vp)]
+        L.h2_matvec.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
+        L.h2_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
+        L.h2_get_tree.argtypes = [_vp] + [_c_i32] * 7 + [_c_d]
+        L.h2_get_blocks.argtypes = [_vp] + [_c_i32] * 4
+        L.h2_get_psi.argtypes = [_vp, _c_d]
+        L.h2_device_status.argtypes = [_vp]
+        L.h2_free.argtypes = [_vp]
+        for f in ("h2_build_geometry", "h2_assemble", "h2_matvec", "h2_stats", "h2_get_tree",
+                  "h2_get_blocks", "h2_get_psi", "h2_device_status", "h2_free"):
+            getattr(L, f).restype = ctypes.c_int
+        _LIB = L
+        return L
+
+
+def lib():
+    return load()
+
+
+def h2_error_string(code: int) -> str:
+    return lib().h2_error_string(int(code)).decode()
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise H2Error(code, where)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def h2_default_params(**kw) -> Params:
+    p = Params()
+    lib().h2_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "rho":
+            k = "box_inflation"
+        setattr(p, k, v)
+    return p
+
+
+def h2_build_geometry(xyz, tri, stream=None) -> int:
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    h = _vp()
+    _check(lib().h2_build_geometry(xyz.ctypes.data_as(_c_d), xyz.shape[0], tri.ctypes.data_as(_c_i32),
+                                   tri.shape[0], _stream_ptr(stream), ctypes.byref(h)),
+           "h2_build_geometry")
+    return h.value
+
+
+def h2_assemble(geom: int, params: Params | None = None) -> int:
+    h = _vp()
+    _check(lib().h2_assemble(geom, ctypes.byref(params) if params is not None else None,
+                             ctypes.byref(h)), "h2_assemble")
+    return h.value
+
+
+def h2_matvec(op: int, u1_ptr: int, u2_ptr: int, r: int, stream=None) -> None:
+    """u2 = M u1 on raw pointers (both device or both host), r x N row-major FP64."""
+    _check(lib().h2_matvec(op, u1_ptr, u2_ptr, int(r), _stream_ptr(stream) if stream != 0 else 0),
+           "h2_matvec")
+
+
+def h2_stats(op: int) -> dict:
+    s = Stats()
+    _check(lib().h2_stats(op, ctypes.byref(s)), "h2_stats")
+    return s.as_dict()
+
+
+def h2_get_tree(op: int) -> dict:
+    st = h2_stats(op)
+    nc, N = st["n_clusters"], st["n_vertices"]
+    out = {k: np.zeros(nc, dtype=np.int32) for k in ("start", "size", "parent", "child0", "child1", "level")}
+    perm = np.zeros(N, dtype=np.int32)
+    box = np.zeros((nc, 6))
+    p = lambda a: a.ctypes.data_as(_c_i32)  # noqa: E731
+    _check(lib().h2_get_tree(op, p(perm), p(out["start"]), p(out["size"]), p(out["parent"]),
+                             p(out["child0"]), p(out["child1"]), p(out["level"]),
+                             box.ctypes.data_as(_c_d)), "h2_get_tree")
+    out["perm"] = perm
+    out["box"] = box
+    return out
+
+
+def h2_get_blocks(op: int) -> dict:
+    st = h2_stats(op)
+    nf, nn = st["n_far_blocks"], st["n_near_blocks"]
+    out = {"far_t": np.zeros(nf, np.int32), "far_s": np.zeros(nf, np.int32),
+           "near_t": np.zeros(nn, np.int32), "near_s": np.zeros(nn, np.int32)}
+    p = lambda a: a.ctypes.data_as(_c_i32)  # noqa: E731
+    _check(lib().h2_get_blocks(op, p(out["far_t"]), p(out["far_s"]), p(out["near_t"]),
+                               p(out["near_s"])), "h2_get_blocks")
+    return out
+
+
+def h2_get_psi(h: int, n: int) -> np.ndarray:
+    out = np.zeros(n)
+    _check(lib().h2_get_psi(h, out.ctypes.data_as(_c_d)), "h2_get_psi")
+    return out
+
+
+def h2_device_status(op: int) -> int:
+    return int(lib().h2_device_status(op))
+
+
+def h2_free(h: int) -> None:
+    if h:
+        _check(lib().h2_free(h), "h2_free")
+
+
+class Geometry:
+    """Closed, outward-oriented triangle surface mesh on the GPU."""
+
+    def __init__(self, xyz, tri, stream=None):
+        self.xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self.tri = np.ascontiguousarray(tri, dtype=np.int32)
+        self.N = int(self.xyz.shape[0])
+        self.handle = h2_build_geometry(self.xyz, self.tri, stream)
+
+    def psi(self) -> np.ndarray:
+        return h2_get_psi(self.handle, self.N)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            h2_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Operator:
+    """H2 approximation of M = K + D on one GPU."""
+
+    def __init__(self, geom: Geometry, m: int = 4, leaf: int = 64, eta: float = 2.0,
+                 rho: float = 0.25, precision: int = FP64, max_rhs: int = 1):
+        self.geom = geom
+        self.N = geom.N
+        self.params = h2_default_params(m=m, leaf=leaf, eta=eta, box_inflation=rho,
+                                        precision=precision, max_rhs=max_rhs)
+        self.handle = h2_assemble(geom.handle, self.params)
+
+    def stats(self) -> dict:
+        return h2_stats(self.handle)
+
+    def tree(self) -> dict:
+        return h2_get_tree(self.handle)
+
+    def blocks(self) -> dict:
+        return h2_get_blocks(self.handle)
+
+    def matvec(self, u1, u2=None, stream=None):
+        """u2 = M u1.  ``u1`` is a (r, N) or (N,) FP64 torch CUDA tensor or numpy array.
+
+        Torch tensors stay on the device (asynchronous on ``stream``); numpy
+        arrays go through the library's synchronous host-pointer path.
+        """
+        if isinstance(u1, np.ndarray):
+            x = np.ascontiguousarray(np.atleast_2d(u1), dtype=np.float64)
+            y = np.empty_like(x) if u2 is None else u2
+            h2_matvec(self.handle, x.ctypes.data, y.ctypes.data, x.shape[0], stream)
+            return y if u1.ndim == 2 else y[0]
+        import torch
+        if u1.dtype != torch.float64 or not u1.is_cuda or not u1.is_contiguous():
+            raise ValueError("u1 must be a contiguous float64 CUDA tensor")
+        x = u1 if u1.dim() == 2 else u1.view(1, -1)
+        if x.shape[1] != self.N:
+            raise ValueError(f"u1 has {x.shape[1]} columns, the mesh has {self.N} nodes")
+        y = torch.empty_like(x) if u2 is None else u2.view(x.shape)
+        h2_matvec(self.handle, x.data_ptr(), y.data_ptr(), x.shape[0], stream)
+        return y if u1.dim() == 2 else y.view(-1)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            h2_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

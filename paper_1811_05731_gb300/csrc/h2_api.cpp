@@ -1,0 +1,297 @@
+// C ABI of the h2bem library (declared in include/h2bem.h).  Argument checks,
+// handle life cycle and host <-> device staging; the numeric work is in
+// h2_assemble.cu and h2_matvec.cu.
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "h2_internal.h"
+
+namespace h2 {
+static thread_local std::string g_last_error;
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+}  // namespace h2
+
+namespace {
+
+void free_device(h2_handle* h) {
+    auto f = [](void* p) {
+        if (p) cudaFree(p);
+    };
+    if (h->kind == 1) {
+        f(h->d_xyz); f(h->d_tri); f(h->d_adj_ptr); f(h->d_adj); f(h->d_psi);
+    } else {
+        h2::release_graph(h);
+        h2::release_profile(h);
+        for (h2::Pass& p : h->passes) { f(p.d_seg); f(p.d_chunk); f(p.d_piece); }
+        f(h->d_arena); f(h->d_perm); f(h->d_box); f(h->d_ws); f(h->d_zero_rows); f(h->d_io); f(h->d_err);
+    }
+}
+
+void release(h2_handle* h) {
+    if (!h) return;
+    if (--h->refcount > 0) return;
+    h2_handle* g = h->kind == 2 ? h->geom : nullptr;
+    free_device(h);
+    delete h;
+    if (g) release(g);
+}
+
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+void h2_default_params(h2_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->m = 4;
+    p->leaf = 64;
+    p->eta = 2.0;
+    p->box_inflation = 0.25;
+    p->precision = H2_FP64;
+    p->max_rhs = 1;
+}
+
+const char* h2_error_string(int code) {
+    switch (code) {
+        case H2_OK: return "ok";
+        case H2_ERR_INVALID_ARG: return "invalid argument";
+        case H2_ERR_MESH_OPEN: return "mesh is not a closed 2-manifold";
+        case H2_ERR_MESH_ORIENTATION: return "mesh orientation is inconsistent or inward";
+        case H2_ERR_DEGENERATE_TRIANGLE: return "degenerate triangle";
+        case H2_ERR_OOM: return "out of memory";
+        case H2_ERR_CUDA: return "CUDA error";
+        case H2_ERR_TIMEOUT: return "device-side wait timed out";
+        case H2_ERR_RHS_EXCEEDS_MAX: return "number of right-hand sides exceeds max_rhs";
+        case H2_ERR_WRONG_HANDLE: return "wrong handle kind";
+        default: return "unknown status";
+    }
+}
+
+const char* h2_last_error_message(void) { return h2::g_last_error.c_str(); }
+
+int h2_build_geometry(const double* xyz, int64_t n_vertices, const int32_t* tri, int64_t n_triangles,
+                      void* cuda_stream, h2_handle** out_geom) {
+    if (!xyz || !tri || !out_geom) return H2_ERR_INVALID_ARG;
+    *out_geom = nullptr;
+    h2_handle* g = new (std::nothrow) h2_handle();
+    if (!g) return H2_ERR_OOM;
+    g->kind = 1;
+    int rc = h2::validate_mesh(xyz, n_vertices, tri, n_triangles, g->adj_ptr, g->adj);
+    if (rc != H2_OK) {
+        delete g;
+        return rc;
+    }
+    g->N = n_vertices;
+    g->T = n_triangles;
+    g->xyz.assign(xyz, xyz + 3 * n_vertices);
+    g->tri.assign(tri, tri + 3 * n_triangles);
+    cudaGetDevice(&g->device);
+    rc = h2::geometry_device_setup(g, (cudaStream_t)cuda_stream);
+    if (rc != H2_OK) {
+        free_device(g);
+        delete g;
+        return rc;
+    }
+    *out_geom = g;
+    return H2_OK;
+}
+
+int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_op) {
+    if (!geom_c || !out_op) return H2_ERR_INVALID_ARG;
+    *out_op = nullptr;
+    if (geom_c->kind != 1) return H2_ERR_WRONG_HANDLE;
+    h2_params p;
+    if (p_in) p = *p_in;
+    else h2_default_params(&p);
+    if (p.m < 1 || p.m > H2_MAX_M || p.leaf < 1 || p.leaf > H2_MAX_LEAF || !(p.eta > 0.0) ||
+        !(p.box_inflation > 0.0) || p.box_inflation > 1.0 || p.max_rhs < 1 || p.max_rhs > H2_MAX_RHS ||
+        (p.precision != H2_FP64 && p.precision != H2_FP32))
+        return H2_ERR_INVALID_ARG;
+    for (int i = 0; i < 4; ++i)
+        if (p.reserved[i] != 0) return H2_ERR_INVALID_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    h2_handle* geom = const_cast<h2_handle*>(geom_c);
+    h2_handle* op = new (std::nothrow) h2_handle();
+    if (!op) return H2_ERR_OOM;
+    op->kind = 2;
+    op->geom = geom;
+    geom->refcount++;
+    op->params = p;
+    op->m = p.m;
+    op->k = p.m * p.m * p.m;
+    op->kp = (op->k + 1) / 2 * 2;
+    op->device = geom->device;
+    h2::build_cluster_tree(op);
+    h2::build_block_partition(op);
+    h2::build_plan(op);
+    int rc = h2::upload_plan(op);
+    if (rc == H2_OK) rc = h2::assemble_device(op, nullptr);
+    if (rc != H2_OK) {
+        release(op);
+        return rc;
+    }
+    op->assemble_seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out_op = op;
+    return H2_OK;
+}
+
+int h2_matvec(h2_handle* op, const double* u1, double* u2, int32_t r, void* cuda_stream) {
+    if (!op || !u1 || !u2) return H2_ERR_INVALID_ARG;
+    if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
+    if (r < 1) return H2_ERR_INVALID_ARG;
+    if (r > op->params.max_rhs) return H2_ERR_RHS_EXCEEDS_MAX;
+    const int64_t N = op->geom->N;
+    const size_t bytes = sizeof(double) * (size_t)N * r;
+    const char *a = (const char*)u1, *b = (const char*)u2;
+    if (a < b + bytes && b < a + bytes) return H2_ERR_INVALID_ARG;   // overlap
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const bool dev1 = is_device_pointer(u1), dev2 = is_device_pointer(u2);
+    if (dev1 != dev2) return H2_ERR_INVALID_ARG;
+    if (dev1) return h2::matvec_device(op, u1, u2, r, s);
+    // host buffers: stage through device memory, synchronous
+    if (!op->d_io) H2_CUDA_TRY(cudaMalloc((void**)&op->d_io, 2 * sizeof(double) * (size_t)N * op->params.max_rhs));
+    double* d1 = op->d_io;
+    double* d2 = op->d_io + (size_t)N * op->params.max_rhs;
+    H2_CUDA_TRY(cudaMemcpyAsync(d1, u1, bytes, cudaMemcpyHostToDevice, s));
+    int rc = h2::matvec_device(op, d1, d2, r, s);
+    if (rc != H2_OK) return rc;
+    H2_CUDA_TRY(cudaMemcpyAsync(u2, d2, bytes, cudaMemcpyDeviceToHost, s));
+    H2_CUDA_TRY(cudaStreamSynchronize(s));
+    int err = 0;
+    H2_CUDA_TRY(cudaMemcpy(&err, op->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    return err ? H2_ERR_TIMEOUT : H2_OK;
+}
+
+int h2_device_status(h2_handle* op) {
+    if (!op) return H2_ERR_INVALID_ARG;
+    if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
+    int err = 0;
+    H2_CUDA_TRY(cudaDeviceSynchronize());
+    H2_CUDA_TRY(cudaMemcpy(&err, op->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        H2_CUDA_TRY(cudaMemset(op->d_err, 0, sizeof(int)));
+        return H2_ERR_TIMEOUT;
+    }
+    return H2_OK;
+}
+
+int h2_profile_enable(h2_handle* op, int32_t enable) {
+    if (!op) return H2_ERR_INVALID_ARG;
+    if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
+    std::vector<double> ms;
+    int n = 0;
+    int rc = h2::read_profile(op, ms, n);   // drops what was recorded so far
+    if (rc != H2_OK) return rc;
+    op->prof_enabled = enable ? 1 : 0;
+    return H2_OK;
+}
+
+int h2_profile_read(h2_handle* op, int32_t capacity, int32_t* kind, double* ms_total, int64_t* bytes,
+                    int64_t* macs, int32_t* grid, int32_t* n_calls, int32_t* n_entries) {
+    if (!op || !n_calls || !n_entries) return H2_ERR_INVALID_ARG;
+    if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
+    std::vector<double> ms;
+    int n = 0;
+    int rc = h2::read_profile(op, ms, n);
+    if (rc != H2_OK) return rc;
+    *n_calls = n;
+    *n_entries = (int32_t)ms.size();
+    for (int32_t i = 0; i < (int32_t)ms.size() && i < capacity; ++i) {
+        const bool pro = i == 0;
+        const h2::Pass* p = pro ? nullptr : &op->passes[(size_t)i - 1];
+        if (kind) kind[i] = pro ? h2::PASS_PROLOGUE : p->kind;
+        if (ms_total) ms_total[i] = ms[(size_t)i];
+        if (bytes) bytes[i] = pro ? 0 : p->bytes;
+        if (macs) macs[i] = pro ? 0 : p->macs;
+        if (grid) grid[i] = pro ? 0 : p->grid;
+    }
+    return H2_OK;
+}
+
+int h2_stats(const h2_handle* op, h2_stats_t* out) {
+    if (!op || !out) return H2_ERR_INVALID_ARG;
+    if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
+    std::memset(out, 0, sizeof(*out));
+    const int64_t N = op->geom->N;
+    out->n_vertices = N;
+    out->n_triangles = op->geom->T;
+    out->n_clusters = op->nc;
+    out->n_levels = op->nlevels;
+    out->n_leaves = op->nleaves;
+    out->k = op->k;
+    out->n_far_blocks = (int64_t)op->far_t.size();
+    out->n_near_blocks = (int64_t)op->near_t.size();
+    out->near_entries = op->near_entries;
+    out->far_coefficients = (int64_t)op->far_t.size() * op->k * op->k;
+    out->basis_coefficients = op->basis_coefficients;
+    out->bytes_far = op->far_bytes;
+    out->bytes_near = op->near_bytes;
+    out->bytes_streamed = op->bytes_streamed;
+    out->macs_per_rhs = op->macs;
+    out->compression_ratio = 1.0 - (double)op->arena_bytes / (8.0 * (double)N * (double)N);
+    out->assemble_seconds = op->assemble_seconds;
+    out->precision = op->params.precision;
+    out->max_rhs = op->params.max_rhs;
+    out->n_launches_matvec = op->n_launches;
+    out->n_passes = (int32_t)op->passes.size();
+    return H2_OK;
+}
+
+int h2_get_tree(const h2_handle* op, int32_t* perm, int32_t* start, int32_t* size, int32_t* parent,
+                int32_t* child0, int32_t* child1, int32_t* level, double* box) {
+    if (!op) return H2_ERR_INVALID_ARG;
+    if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
+    auto cp = [](void* dst, const void* src, size_t n) {
+        if (dst) std::memcpy(dst, src, n);
+    };
+    cp(perm, op->perm.data(), sizeof(int32_t) * op->perm.size());
+    cp(start, op->start.data(), sizeof(int32_t) * op->nc);
+    cp(size, op->size.data(), sizeof(int32_t) * op->nc);
+    cp(parent, op->parent.data(), sizeof(int32_t) * op->nc);
+    cp(child0, op->child0.data(), sizeof(int32_t) * op->nc);
+    cp(child1, op->child1.data(), sizeof(int32_t) * op->nc);
+    cp(level, op->level.data(), sizeof(int32_t) * op->nc);
+    cp(box, op->box.data(), sizeof(double) * 6 * op->nc);
+    return H2_OK;
+}
+
+int h2_get_blocks(const h2_handle* op, int32_t* far_t, int32_t* far_s, int32_t* near_t, int32_t* near_s) {
+    if (!op) return H2_ERR_INVALID_ARG;
+    if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
+    auto cp = [](int32_t* dst, const std::vector<int32_t>& v) {
+        if (dst && !v.empty()) std::memcpy(dst, v.data(), sizeof(int32_t) * v.size());
+    };
+    cp(far_t, op->far_t);
+    cp(far_s, op->far_s);
+    cp(near_t, op->near_t);
+    cp(near_s, op->near_s);
+    return H2_OK;
+}
+
+int h2_get_psi(const h2_handle* h, double* psi) {
+    if (!h || !psi) return H2_ERR_INVALID_ARG;
+    const h2_handle* g = h->kind == 2 ? h->geom : h;
+    H2_CUDA_TRY(cudaMemcpy(psi, g->d_psi, sizeof(double) * g->N, cudaMemcpyDeviceToHost));
+    return H2_OK;
+}
+
+int h2_free(h2_handle* h) {
+    if (!h) return H2_OK;
+    if (h->kind != 1 && h->kind != 2) return H2_ERR_WRONG_HANDLE;
+    release(h);
+    return H2_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,516 @@
+// Device-side assembly of the boundary operator M = K + D (arXiv:1811.05731,
+// Eq. matrix_definition / Eq. denseMat) in H2 form (Section "H2-Matrix
+// Compression").  Everything numeric is computed here in FP64; far-field
+// matrices are rounded to FP32 on store when the operator is built in FP32.
+//
+//   k_psi        interior solid angle Psi_i at every node (Eq. mainInt)
+//   k_leaf_V     V_t(i, nu)  = L^t_nu(xi_i)                     (row basis)
+//   k_leaf_W     W_s(j, mu)  = oint phi_j n . grad L^s_mu dS    (column basis)
+//   k_transfer   E_c(nu', nu) = L^parent_nu(x^c_nu')            (nested bases)
+//   k_coupling   S_ts(nu, mu) = 1 / (4 pi |x^t_nu - x^s_mu|)
+//   k_near       K_ij (Lindholm's closed form) + D_ii on inadmissible leaf pairs
+//
+// Sign convention of the double-layer term: K_ij = (1/4pi) oint phi_j(y)
+// n_y . (xi_i - y) / |xi_i - y|^3 dS_y, under which a constant u1 gives
+// u2 = -u1 (the row sums of M are -1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "h2_internal.h"
+
+namespace h2 {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct d3 {
+    double x, y, z;
+};
+__device__ __forceinline__ d3 mk(const double* p) { return {p[0], p[1], p[2]}; }
+__device__ __forceinline__ d3 operator-(d3 a, d3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ d3 operator+(d3 a, d3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ d3 operator*(double s, d3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ d3 cross(d3 a, d3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ double norm(d3 a) { return sqrt(dot(a, a)); }
+
+// ---------------------------------------------------------------------------
+// Psi_i: interior solid angle of the surface at node i.  For a closed,
+// embedded polyhedral surface the solid angle that all other triangles
+// subtend at a node equals the area of the spherical polygon cut out of the
+// unit sphere around the node by its fan of triangles.  With the link
+// directions u_a (unit vectors to the rim nodes, in the cyclic order given by
+// the outward-oriented triangles (i, a, b)), Gauss-Bonnet gives the area on
+// the exterior side as 2 pi - sum of turning angles, so the interior angle is
+//     Psi_i = 2 pi + sum_b theta_b,
+//     theta_b = atan2(det(N1, N2, u_b), N1 . N2),  N1 = u_a x u_b, N2 = u_b x u_c,
+// for consecutive rim nodes a -> b -> c.  (A flat node gives 2 pi, a cube
+// corner pi / 2.)
+// ---------------------------------------------------------------------------
+__global__ void k_psi(int64_t N, const double* __restrict__ xyz, const int32_t* __restrict__ tri,
+                      const int64_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                      double* __restrict__ psi) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const d3 xi = mk(xyz + 3 * i);
+    const int64_t p0 = adj_ptr[i], p1 = adj_ptr[i + 1];
+    double sum = 0.0;
+    for (int64_t p = p0; p < p1; ++p) {
+        const int32_t* v = tri + 3 * (int64_t)adj[p];
+        const int c = v[0] == i ? 0 : (v[1] == i ? 1 : 2);
+        const int32_t a = v[(c + 1) % 3], b = v[(c + 2) % 3];
+        int32_t cnext = -1;
+        for (int64_t q = p0; q < p1; ++q) {
+            const int32_t* w = tri + 3 * (int64_t)adj[q];
+            const int cc = w[0] == i ? 0 : (w[1] == i ? 1 : 2);
+            if (w[(cc + 1) % 3] == b) { cnext = w[(cc + 2) % 3]; break; }
+        }
+        if (cnext < 0) continue;   // rejected by the host-side mesh check
+        d3 ua = mk(xyz + 3 * (int64_t)a) - xi, ub = mk(xyz + 3 * (int64_t)b) - xi,
+           uc = mk(xyz + 3 * (int64_t)cnext) - xi;
+        ua = (1.0 / norm(ua)) * ua;
+        ub = (1.0 / norm(ub)) * ub;
+        uc = (1.0 / norm(uc)) * uc;
+        const d3 n1 = cross(ua, ub), n2 = cross(ub, uc);
+        sum += atan2(dot(cross(n1, n2), ub), dot(n1, n2));
+    }
+    psi[i] = 2.0 * kPi + sum;
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev interpolation on an axis-parallel box: m points of the first kind
+// per axis, c + (w/2) cos((2j+1) pi / (2m)), tensor index nu = (a m + b) m + c.
+// ---------------------------------------------------------------------------
+struct Cheb {
+    double p[3][H2_MAX_M];
+};
+
+__device__ __forceinline__ void cheb_nodes(const double* box, int m, Cheb& cb) {
+    for (int d = 0; d < 3; ++d) {
+        const double c = 0.5 * (box[d] + box[3 + d]), h = 0.5 * (box[3 + d] - box[d]);
+        for (int j = 0; j < m; ++j) cb.p[d][j] = c + h * cos((2.0 * j + 1.0) * kPi / (2.0 * m));
+    }
+}
+
+// Lagrange polynomial of node j among p[0..m-1] at t.
+__device__ __forceinline__ double lagr(const double* p, int m, int j, double t) {
+    double v = 1.0;
+    for (int l = 0; l < m; ++l)
+        if (l != j) v *= (t - p[l]) / (p[j] - p[l]);
+    return v;
+}
+// Its derivative: sum over the dropped factor q of the remaining product.
+__device__ __forceinline__ double dlagr(const double* p, int m, int j, double t) {
+    double s = 0.0;
+    for (int q = 0; q < m; ++q) {
+        if (q == j) continue;
+        double v = 1.0 / (p[j] - p[q]);
+        for (int l = 0; l < m; ++l)
+            if (l != j && l != q) v *= (t - p[l]) / (p[j] - p[l]);
+        s += v;
+    }
+    return s;
+}
+
+__device__ __forceinline__ void store(unsigned char* arena, int64_t off, int64_t idx, double v,
+                                      int f32) {
+    if (f32) reinterpret_cast<float*>(arena + off)[idx] = (float)v;
+    else reinterpret_cast<double*>(arena + off)[idx] = v;
+}
+
+struct BasisItem {
+    double box[6];
+    int64_t off;
+    int32_t start, size;
+};
+
+// V_t (|t| x k, column-major: (a, nu) at nu*|t| + a).
+__global__ void k_leaf_V(const BasisItem* __restrict__ items, int m, const int32_t* __restrict__ perm,
+                         const double* __restrict__ xyz, unsigned char* arena, int f32) {
+    const BasisItem it = items[blockIdx.x];
+    const int k = m * m * m;
+    const int nu = threadIdx.x;
+    if (nu >= k) return;
+    Cheb cb;
+    cheb_nodes(it.box, m, cb);
+    const int a = nu / (m * m), b = (nu / m) % m, c = nu % m;
+    for (int q = 0; q < it.size; ++q) {
+        const double* x = xyz + 3 * (int64_t)perm[it.start + q];
+        const double v = lagr(cb.p[0], m, a, x[0]) * lagr(cb.p[1], m, b, x[1]) *
+                         lagr(cb.p[2], m, c, x[2]);
+        store(arena, it.off, (int64_t)nu * it.size + q, v, f32);
+    }
+}
+
+// W_s (k x |s| column-major: (mu, j) at j*k + mu), the integral of phi_j
+// n . grad L_mu over the triangles around node j by a collapsed (Duffy)
+// Gauss-Legendre product rule with q points per direction, exact for the
+// polynomial integrand of total degree 3(m-1) when 2q - 1 >= 3m - 2.
+__global__ void k_leaf_W(const BasisItem* __restrict__ items, int m, const int32_t* __restrict__ perm,
+                         const double* __restrict__ xyz, const int32_t* __restrict__ tri,
+                         const int64_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                         const double* __restrict__ gx, const double* __restrict__ gw, int q,
+                         unsigned char* arena, int f32) {
+    const BasisItem it = items[blockIdx.x];
+    const int k = m * m * m;
+    const int mu = threadIdx.x;
+    if (mu >= k) return;
+    Cheb cb;
+    cheb_nodes(it.box, m, cb);
+    const int a = mu / (m * m), b = (mu / m) % m, c = mu % m;
+    for (int jl = 0; jl < it.size; ++jl) {
+        const int32_t j = perm[it.start + jl];
+        double acc = 0.0;
+        for (int64_t p = adj_ptr[j]; p < adj_ptr[j + 1]; ++p) {
+            const int32_t* v = tri + 3 * (int64_t)adj[p];
+            const int cj = v[0] == j ? 0 : (v[1] == j ? 1 : 2);
+            const d3 r0 = mk(xyz + 3 * (int64_t)v[0]), r1 = mk(xyz + 3 * (int64_t)v[1]),
+                     r2 = mk(xyz + 3 * (int64_t)v[2]);
+            const d3 e1 = r1 - r0, e2 = r2 - r0;
+            const d3 nn = cross(e1, e2);
+            const double twoA = norm(nn);
+            const d3 n = (1.0 / twoA) * nn;
+            for (int iu = 0; iu < q; ++iu) {
+                const double s = gx[iu];
+                for (int iv = 0; iv < q; ++iv) {
+                    const double t = gx[iv] * (1.0 - s);
+                    const double wt = gw[iu] * gw[iv] * (1.0 - s) * twoA;
+                    const double phi = cj == 0 ? 1.0 - s - t : (cj == 1 ? s : t);
+                    const d3 y = r0 + (s * e1 + t * e2);
+                    const double lx = lagr(cb.p[0], m, a, y.x), ly = lagr(cb.p[1], m, b, y.y),
+                                 lz = lagr(cb.p[2], m, c, y.z);
+                    const double gxv = dlagr(cb.p[0], m, a, y.x) * ly * lz;
+                    const double gyv = lx * dlagr(cb.p[1], m, b, y.y) * lz;
+                    const double gzv = lx * ly * dlagr(cb.p[2], m, c, y.z);
+                    acc += wt * phi * (n.x * gxv + n.y * gyv + n.z * gzv);
+                }
+            }
+        }
+        store(arena, it.off, (int64_t)jl * k + mu, acc, f32);
+    }
+}
+
+struct TransferItem {
+    double box_child[6], box_parent[6];
+    int64_t off_up, off_down;   // -1 when not stored
+};
+
+// E_c(nu', nu) = L^parent_nu(x^c_nu').  Up layout (nu, nu') at nu'*k + nu,
+// down layout (nu', nu) at nu*k + nu'.
+__global__ void k_transfer(const TransferItem* __restrict__ items, int m, unsigned char* arena,
+                           int f32) {
+    const TransferItem& it = items[blockIdx.x];
+    const int k = m * m * m;
+    const int nu = threadIdx.x;
+    if (nu >= k) return;
+    Cheb cc, cp;
+    cheb_nodes(it.box_child, m, cc);
+    cheb_nodes(it.box_parent, m, cp);
+    const int a = nu / (m * m), b = (nu / m) % m, c = nu % m;
+    for (int np = 0; np < k; ++np) {
+        const int a2 = np / (m * m), b2 = (np / m) % m, c2 = np % m;
+        const double v = lagr(cp.p[0], m, a, cc.p[0][a2]) * lagr(cp.p[1], m, b, cc.p[1][b2]) *
+                         lagr(cp.p[2], m, c, cc.p[2][c2]);
+        if (it.off_up >= 0) store(arena, it.off_up, (int64_t)np * k + nu, v, f32);
+        if (it.off_down >= 0) store(arena, it.off_down, (int64_t)nu * k + np, v, f32);
+    }
+}
+
+struct CouplingItem {
+    int32_t t, s;
+    int64_t off;
+};
+
+// S_ts (k x k column-major: (nu, mu) at mu*k + nu).
+__global__ void k_coupling(const CouplingItem* __restrict__ items, int m,
+                           const double* __restrict__ box, unsigned char* arena, int f32) {
+    const CouplingItem it = items[blockIdx.x];
+    const int k = m * m * m;
+    __shared__ double pt[3][H2_MAX_K], ps[3][H2_MAX_K];
+    __shared__ Cheb ct, cs;
+    if (threadIdx.x == 0) {
+        cheb_nodes(box + 6 * (int64_t)it.t, m, ct);
+        cheb_nodes(box + 6 * (int64_t)it.s, m, cs);
+    }
+    __syncthreads();
+    for (int nu = threadIdx.x; nu < k; nu += blockDim.x) {
+        const int a = nu / (m * m), b = (nu / m) % m, c = nu % m;
+        pt[0][nu] = ct.p[0][a]; pt[1][nu] = ct.p[1][b]; pt[2][nu] = ct.p[2][c];
+        ps[0][nu] = cs.p[0][a]; ps[1][nu] = cs.p[1][b]; ps[2][nu] = cs.p[2][c];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+        const int mu = idx / k, nu = idx % k;
+        const double dx = pt[0][nu] - ps[0][mu], dy = pt[1][nu] - ps[1][mu],
+                     dz = pt[2][nu] - ps[2][mu];
+        const double v = 1.0 / (4.0 * kPi * sqrt(dx * dx + dy * dy + dz * dz));
+        store(arena, it.off, idx, v, f32);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Lindholm's closed form for a linear basis on a flat triangle.  For the
+// triangle T = (r0, r1, r2) with unit normal n ~ (r1 - r0) x (r2 - r0), area A,
+// edge b from r_b to r_{b+1} (length s_b, direction sh_b) and the observation
+// point x (rho_b = r_b - x, R_b = |rho_b|, zeta = n . rho_0):
+//   P_b     = ln((R_b + R_{b+1} + s_b) / (R_b + R_{b+1} - s_b))
+//   eta_b   = (n x sh_b) . rho_b
+//   Omega   = solid angle of T at x (Van Oosterom-Strackee)
+//   w_a     = s_{a+1} / (8 pi A) [ eta_{a+1} Omega - zeta sum_b (sh_{a+1} . sh_b) P_b ]
+// where w_a = (1/4pi) int_T phi_a n . (x - y) / |x - y|^3 dS_y.  A point in the
+// plane of T (|zeta| <= 1e-13 sqrt(A)) sees no double-layer contribution.
+// ---------------------------------------------------------------------------
+__device__ void lindholm_weights(d3 x, d3 r0, d3 r1, d3 r2, double w[3]) {
+    const d3 r[3] = {r0, r1, r2};
+    d3 rho[3], sh[3];
+    double R[3], sl[3];
+    for (int b = 0; b < 3; ++b) {
+        rho[b] = r[b] - x;
+        R[b] = norm(rho[b]);
+        const d3 e = r[(b + 1) % 3] - r[b];
+        sl[b] = norm(e);
+        sh[b] = (1.0 / sl[b]) * e;
+    }
+    const d3 nn = cross(r1 - r0, r2 - r0);
+    const double twoA = norm(nn);
+    const double A = 0.5 * twoA;
+    const d3 n = (1.0 / twoA) * nn;
+    const double zeta = dot(n, rho[0]);
+    if (fabs(zeta) <= 1e-13 * sqrt(A)) {
+        w[0] = w[1] = w[2] = 0.0;
+        return;
+    }
+    const double num = dot(rho[0], cross(rho[1], rho[2]));
+    const double den = R[0] * R[1] * R[2] + dot(rho[0], rho[1]) * R[2] +
+                       dot(rho[0], rho[2]) * R[1] + dot(rho[1], rho[2]) * R[0];
+    const double omega = 2.0 * atan2(num, den);
+    double P[3], eta[3];
+    for (int b = 0; b < 3; ++b) {
+        const double Rs = R[b] + R[(b + 1) % 3];
+        P[b] = log((Rs + sl[b]) / (Rs - sl[b]));
+        eta[b] = dot(cross(n, sh[b]), rho[b]);
+    }
+    const double pre = 1.0 / (8.0 * kPi * A);
+    for (int a = 0; a < 3; ++a) {
+        const int o = (a + 1) % 3;
+        const double g = dot(sh[o], sh[0]) * P[0] + dot(sh[o], sh[1]) * P[1] +
+                         dot(sh[o], sh[2]) * P[2];
+        w[a] = sl[o] * pre * (eta[o] * omega - zeta * g);
+    }
+}
+
+struct NearItem {
+    int64_t off;
+    int32_t t_start, t_size, s_start, s_size;
+    int32_t tl0, tl1;   // range in the source leaf's triangle list
+    int32_t diag;       // t == s
+    int32_t pad;
+};
+
+struct LeafTri {
+    int32_t tri;
+    int32_t col[3];     // column of each corner in the source leaf, -1 outside
+};
+
+// One near block N_ts (|t| x |s| column-major: (a, b) at b*|t| + a) per CTA;
+// thread a owns row a and sums the corner weights of every triangle around
+// the source leaf into the columns of the corners that belong to s.
+__global__ void k_near(const NearItem* __restrict__ items, const LeafTri* __restrict__ ltri,
+                       const int32_t* __restrict__ perm, const double* __restrict__ xyz,
+                       const int32_t* __restrict__ tri, const double* __restrict__ psi,
+                       unsigned char* arena) {
+    extern __shared__ double blk[];
+    const NearItem it = items[blockIdx.x];
+    const int nt = it.t_size, ns = it.s_size;
+    for (int idx = threadIdx.x; idx < nt * ns; idx += blockDim.x) blk[idx] = 0.0;
+    __syncthreads();
+    const int a = threadIdx.x;
+    if (a < nt) {
+        const int32_t i = perm[it.t_start + a];
+        const d3 x = mk(xyz + 3 * (int64_t)i);
+        for (int e = it.tl0; e < it.tl1; ++e) {
+            const LeafTri lt = ltri[e];
+            const int32_t* v = tri + 3 * (int64_t)lt.tri;
+            if (v[0] == i || v[1] == i || v[2] == i) continue;
+            double w[3];
+            lindholm_weights(x, mk(xyz + 3 * (int64_t)v[0]), mk(xyz + 3 * (int64_t)v[1]),
+                             mk(xyz + 3 * (int64_t)v[2]), w);
+            for (int q = 0; q < 3; ++q)
+                if (lt.col[q] >= 0) blk[lt.col[q] * nt + a] += w[q];
+        }
+        if (it.diag) blk[a * nt + a] += psi[i] / (4.0 * kPi) - 1.0;
+    }
+    __syncthreads();
+    double* out = reinterpret_cast<double*>(arena + it.off);
+    for (int idx = threadIdx.x; idx < nt * ns; idx += blockDim.x) out[idx] = blk[idx];
+}
+
+template <class Tv>
+int upload(const std::vector<Tv>& v, Tv** d, cudaStream_t s) {
+    *d = nullptr;
+    if (v.empty()) return H2_OK;
+    H2_CUDA_TRY(cudaMalloc((void**)d, sizeof(Tv) * v.size()));
+    H2_CUDA_TRY(cudaMemcpyAsync(*d, v.data(), sizeof(Tv) * v.size(), cudaMemcpyHostToDevice, s));
+    return H2_OK;
+}
+
+}  // namespace
+
+int geometry_device_setup(h2_handle* g, cudaStream_t s) {
+    int rc;
+    if ((rc = upload(g->xyz, &g->d_xyz, s))) return rc;
+    if ((rc = upload(g->tri, &g->d_tri, s))) return rc;
+    if ((rc = upload(g->adj_ptr, &g->d_adj_ptr, s))) return rc;
+    if ((rc = upload(g->adj, &g->d_adj, s))) return rc;
+    H2_CUDA_TRY(cudaMalloc((void**)&g->d_psi, sizeof(double) * g->N));
+    const int bs = 128;
+    k_psi<<<(unsigned)((g->N + bs - 1) / bs), bs, 0, s>>>(g->N, g->d_xyz, g->d_tri, g->d_adj_ptr,
+                                                          g->d_adj, g->d_psi);
+    H2_CUDA_TRY(cudaGetLastError());
+    H2_CUDA_TRY(cudaStreamSynchronize(s));
+    return H2_OK;
+}
+
+int assemble_device(h2_handle* op, cudaStream_t s) {
+    const h2_handle* g = op->geom;
+    const int m = op->m, k = op->k;
+    const int f32 = op->params.precision == H2_FP32 ? 1 : 0;
+    int rc;
+
+    H2_CUDA_TRY(cudaMalloc((void**)&op->d_arena, (size_t)std::max<int64_t>(op->arena_bytes, 16)));
+    H2_CUDA_TRY(cudaMemsetAsync(op->d_arena, 0, (size_t)std::max<int64_t>(op->arena_bytes, 16), s));
+    if ((rc = upload(op->perm, &op->d_perm, s))) return rc;
+    if ((rc = upload(op->box, &op->d_box, s))) return rc;
+
+    std::vector<void*> tmp;
+    auto cleanup = [&]() {
+        for (void* p : tmp) cudaFree(p);
+        tmp.clear();
+    };
+
+    // leaf bases
+    std::vector<BasisItem> vi, wi;
+    for (int c = 0; c < op->nc; ++c) {
+        BasisItem it{};
+        std::memcpy(it.box, &op->box[6 * (size_t)c], sizeof(it.box));
+        it.start = op->start[c];
+        it.size = op->size[c];
+        if (op->V[c].off >= 0) { it.off = op->V[c].off; vi.push_back(it); }
+        if (op->W[c].off >= 0) { it.off = op->W[c].off; wi.push_back(it); }
+    }
+    std::vector<double> gx, gw;
+    const int q = (3 * m) / 2;   // ceil((3m - 1) / 2)
+    gauss_legendre_unit(q, gx, gw);
+    BasisItem *d_vi = nullptr, *d_wi = nullptr;
+    double *d_gx = nullptr, *d_gw = nullptr;
+    if ((rc = upload(vi, &d_vi, s)) || (rc = upload(wi, &d_wi, s)) || (rc = upload(gx, &d_gx, s)) ||
+        (rc = upload(gw, &d_gw, s))) {
+        cleanup();
+        return rc;
+    }
+    tmp.insert(tmp.end(), {d_vi, d_wi, d_gx, d_gw});
+    const int kb = (k + 31) / 32 * 32;
+    if (!vi.empty())
+        k_leaf_V<<<(unsigned)vi.size(), kb, 0, s>>>(d_vi, m, op->d_perm, g->d_xyz, op->d_arena, f32);
+    if (!wi.empty())
+        k_leaf_W<<<(unsigned)wi.size(), kb, 0, s>>>(d_wi, m, op->d_perm, g->d_xyz, g->d_tri,
+                                                    g->d_adj_ptr, g->d_adj, d_gx, d_gw, q,
+                                                    op->d_arena, f32);
+
+    // transfers
+    std::vector<TransferItem> ti;
+    for (int c = 0; c < op->nc; ++c) {
+        if (op->Eup[c].off < 0 && op->Edown[c].off < 0) continue;
+        TransferItem it{};
+        std::memcpy(it.box_child, &op->box[6 * (size_t)c], sizeof(it.box_child));
+        std::memcpy(it.box_parent, &op->box[6 * (size_t)op->parent[c]], sizeof(it.box_parent));
+        it.off_up = op->Eup[c].off;
+        it.off_down = op->Edown[c].off;
+        ti.push_back(it);
+    }
+    TransferItem* d_ti = nullptr;
+    if ((rc = upload(ti, &d_ti, s))) { cleanup(); return rc; }
+    tmp.push_back(d_ti);
+    if (!ti.empty()) k_transfer<<<(unsigned)ti.size(), kb, 0, s>>>(d_ti, m, op->d_arena, f32);
+
+    // coupling
+    std::vector<CouplingItem> ci(op->far_t.size());
+    for (size_t b = 0; b < ci.size(); ++b) ci[b] = {op->far_t[b], op->far_s[b], op->S[b].off};
+    CouplingItem* d_ci = nullptr;
+    if ((rc = upload(ci, &d_ci, s))) { cleanup(); return rc; }
+    tmp.push_back(d_ci);
+    if (!ci.empty()) k_coupling<<<(unsigned)ci.size(), 256, 0, s>>>(d_ci, m, op->d_box, op->d_arena, f32);
+
+    // near field: per source leaf, the triangles around its nodes
+    std::vector<int32_t> leaf_pos(op->nc, -1);
+    std::vector<LeafTri> ltri;
+    std::vector<int32_t> ltr0(op->nc, 0), ltr1(op->nc, 0);
+    {
+        std::vector<int32_t> col_of((size_t)g->N, -1);
+        std::vector<int32_t> seen((size_t)g->T, -1);
+        for (int c = 0; c < op->nc; ++c) {
+            if (op->child0[c] >= 0) continue;
+            for (int a = 0; a < op->size[c]; ++a) col_of[op->perm[op->start[c] + a]] = a;
+            ltr0[c] = (int32_t)ltri.size();
+            for (int a = 0; a < op->size[c]; ++a) {
+                const int32_t j = op->perm[op->start[c] + a];
+                for (int64_t p = g->adj_ptr[j]; p < g->adj_ptr[j + 1]; ++p) {
+                    const int32_t t = g->adj[p];
+                    if (seen[t] == c) continue;
+                    seen[t] = c;
+                    LeafTri lt{};
+                    lt.tri = t;
+                    for (int q2 = 0; q2 < 3; ++q2) lt.col[q2] = col_of[g->tri[3 * (size_t)t + q2]];
+                    ltri.push_back(lt);
+                }
+            }
+            ltr1[c] = (int32_t)ltri.size();
+            for (int a = 0; a < op->size[c]; ++a) col_of[op->perm[op->start[c] + a]] = -1;
+        }
+    }
+    std::vector<NearItem> ni(op->near_t.size());
+    int maxleaf = 1;
+    for (size_t b = 0; b < ni.size(); ++b) {
+        const int t = op->near_t[b], sc = op->near_s[b];
+        NearItem it{};
+        it.off = op->Nb[b].off;
+        it.t_start = op->start[t];
+        it.t_size = op->size[t];
+        it.s_start = op->start[sc];
+        it.s_size = op->size[sc];
+        it.tl0 = ltr0[sc];
+        it.tl1 = ltr1[sc];
+        it.diag = t == sc;
+        ni[b] = it;
+        maxleaf = std::max(maxleaf, std::max(it.t_size, it.s_size));
+    }
+    NearItem* d_ni = nullptr;
+    LeafTri* d_lt = nullptr;
+    if ((rc = upload(ni, &d_ni, s)) || (rc = upload(ltri, &d_lt, s))) { cleanup(); return rc; }
+    tmp.insert(tmp.end(), {d_ni, d_lt});
+    if (!ni.empty()) {
+        const size_t smem = sizeof(double) * (size_t)maxleaf * maxleaf;
+        H2_CUDA_TRY(cudaFuncSetAttribute(k_near, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int nb = (maxleaf + 31) / 32 * 32;
+        k_near<<<(unsigned)ni.size(), nb, smem, s>>>(d_ni, d_lt, op->d_perm, g->d_xyz, g->d_tri,
+                                                     g->d_psi, op->d_arena);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return H2_ERR_CUDA;
+    }
+    return H2_OK;
+}
+
+}  // namespace h2

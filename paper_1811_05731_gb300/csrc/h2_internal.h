@@ -1,0 +1,190 @@
+// Internal data structures of the h2bem library (not part of the C ABI).
+//
+// The matrix-vector product u2 = M u1 (Eq. denseMat) with the H2 form of M
+// (Section "H2-Matrix Compression") is executed as a fixed sequence of
+// "passes".  Every pass is a block-sparse product
+//
+//     out_segment (nrows x r)  (=, +=, atomic +=)  sum_pieces A_piece (nrows x ncols) * in_piece (ncols x r)
+//
+// over the FP64 workspace (row-major, r values per row).  All matrices a
+// matvec reads are packed into one byte arena in the exact order in which the
+// passes consume them, so that every pass streams one contiguous range of
+// HBM with bulk (TMA) copies.  The host builds the plan once per operator.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/h2bem.h"
+
+#define H2_MAX_M 5
+#define H2_MAX_K 125
+#define H2_MAX_LEAF 128
+#define H2_MAX_RHS 32
+
+namespace h2 {
+
+enum SegMode : int32_t {
+    SEG_STORE = 0,      // ws[out_row + i] = sum
+    SEG_ATOMIC = 1,     // atomicAdd(ws[out_row + i], sum)
+    SEG_FINAL = 2,      // u2[c * N + perm[out_row + i]] = sum
+    SEG_ADD = 3,        // ws[out_row + i] += sum (single writer per pass)
+};
+
+enum PieceType : int32_t { PIECE_F64 = 0, PIECE_F32 = 1 };
+
+// A contiguous, 16-byte aligned byte range of the arena that one bulk copy
+// brings into one shared-memory stage.  It holds whole small blocks or a
+// column range of one large block ("pieces").
+struct Chunk {
+    int64_t src;         // byte offset in the arena
+    int32_t bytes;       // multiple of 16
+    int32_t piece0;      // first piece (index into the pass's piece array)
+    int32_t npieces;
+    int32_t pad;
+};
+
+// One column-major matrix (nrows x ncols, nrows = the segment's) inside a
+// stage, multiplied with workspace rows [in_row, in_row + ncols).
+struct Piece {
+    int32_t smem_off;    // byte offset inside the stage (16-byte aligned)
+    int32_t in_row;
+    int32_t ncols;
+    int32_t type;        // PieceType
+};
+
+struct Segment {
+    int32_t out_row;     // workspace row (or tree position for SEG_FINAL)
+    int32_t nrows;       // <= 128
+    int32_t mode;        // SegMode
+    int32_t chunk0;      // first chunk
+    int32_t nchunks;
+    int32_t pad;
+};
+
+// Host plan of one pass plus its device copies.
+enum PassKind : int32_t {
+    PASS_PROLOGUE = 0, PASS_UP_LEAF = 1, PASS_UP_TRANSFER = 2, PASS_COUPLING = 3,
+    PASS_DOWN_TRANSFER = 4, PASS_LEAF_NEAR = 5,
+};
+
+struct Pass {
+    std::string name;
+    int32_t kind = 0;
+    std::vector<Segment> seg;
+    std::vector<Chunk> chunk;
+    std::vector<Piece> piece;
+    Segment* d_seg = nullptr;
+    Chunk* d_chunk = nullptr;
+    Piece* d_piece = nullptr;
+    int64_t bytes = 0;        // arena bytes streamed by the pass
+    int64_t macs = 0;         // multiply-adds per right-hand side
+    int grid = 0;
+};
+
+// Where one matrix lives in the arena.
+struct MatRef {
+    int64_t off = -1;   // byte offset, 16-byte aligned
+    int32_t nrows = 0, ncols = 0, type = 0;
+};
+
+}  // namespace h2
+
+struct h2_handle {
+    int kind = 0;   // 1 geometry, 2 operator
+    int refcount = 1;
+
+    // ---------------- geometry ----------------
+    int64_t N = 0, T = 0;
+    std::vector<double> xyz;        // host copy, N x 3
+    std::vector<int32_t> tri;       // host copy, T x 3
+    std::vector<int64_t> adj_ptr;   // node -> triangles (CSR)
+    std::vector<int32_t> adj;
+    double* d_xyz = nullptr;
+    int32_t* d_tri = nullptr;
+    int64_t* d_adj_ptr = nullptr;
+    int32_t* d_adj = nullptr;
+    double* d_psi = nullptr;
+    int device = 0;
+
+    // ---------------- operator ----------------
+    h2_handle* geom = nullptr;
+    h2_params params{};
+    int m = 0, k = 0, kp = 0;       // kp = k rounded up to even (workspace row alignment)
+    // cluster tree (host), numbered level by level
+    int nc = 0, nlevels = 0, nleaves = 0;
+    std::vector<int32_t> perm, start, size, parent, child0, child1, level;
+    std::vector<double> box;        // 6 per cluster: lo xyz, hi xyz
+    std::vector<int32_t> far_t, far_s, near_t, near_s;
+    std::vector<char> need_x, need_y, is_src, is_tgt;
+    // matrices
+    std::vector<h2::MatRef> W, V, Eup, Edown;     // per cluster
+    std::vector<h2::MatRef> S;                    // per far block
+    std::vector<h2::MatRef> Nb;                   // per near block
+    int64_t arena_bytes = 0;
+    unsigned char* d_arena = nullptr;
+    int32_t* d_perm = nullptr;
+    double* d_box = nullptr;
+    // workspace rows: [0, N) permuted input, then x-hat and y-hat (kp rows per cluster)
+    int64_t row_xhat = 0, row_yhat = 0, ws_rows = 0;
+    double* d_ws = nullptr;
+    std::vector<int32_t> zero_rows;   // y-hat regions cleared before the coupling pass
+    int32_t* d_zero_rows = nullptr;
+    double* d_io = nullptr;           // device staging for host-pointer calls
+    int* d_err = nullptr;             // device error word (bounded waits)
+    // passes in launch order
+    std::vector<h2::Pass> passes;
+    int64_t bytes_streamed = 0, macs = 0;
+    int64_t far_bytes = 0, near_bytes = 0, basis_coefficients = 0, near_entries = 0;
+    double assemble_seconds = 0.0;
+    int stages = 4;                   // shared-memory stages of the pass kernel
+    int stage_bytes = 32768;
+    // CUDA graph of one matvec (rebuilt when r changes)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_r = 0;
+    const double* graph_u1 = nullptr;
+    double* graph_u2 = nullptr;
+    cudaGraphNode_t node_first = nullptr, node_last = nullptr;
+    int n_launches = 0;
+    // per-pass timing with CUDA events (profiling aid, off by default)
+    int prof_enabled = 0;
+    std::vector<std::vector<cudaEvent_t>> prof_calls;   // events of each profiled call
+    std::vector<cudaEvent_t> prof_pool;
+};
+
+namespace h2 {
+// host-side builders (h2_host.cpp)
+int validate_mesh(const double* xyz, int64_t N, const int32_t* tri, int64_t T,
+                  std::vector<int64_t>& adj_ptr, std::vector<int32_t>& adj);
+void build_cluster_tree(h2_handle* op);
+void build_block_partition(h2_handle* op);
+void gauss_legendre_unit(int q, std::vector<double>& x, std::vector<double>& w);
+void build_plan(h2_handle* op);   // arena layout + passes (h2_plan.cpp)
+
+// device-side assembly and matvec (h2_assemble.cu, h2_matvec.cu)
+int geometry_device_setup(h2_handle* g, cudaStream_t s);
+int assemble_device(h2_handle* op, cudaStream_t s);
+int upload_plan(h2_handle* op);
+int matvec_device(h2_handle* op, const double* u1, double* u2, int r, cudaStream_t s);
+void release_graph(h2_handle* op);
+void release_profile(h2_handle* op);
+int read_profile(h2_handle* op, std::vector<double>& ms, int& ncalls);
+size_t pass_smem_bytes(const h2_handle* op, int rt);
+}  // namespace h2
+
+#define H2_CUDA_TRY(call)                                        \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) {                                 \
+            h2::set_last_error(cudaGetErrorString(e_));          \
+            return e_ == cudaErrorMemoryAllocation ? H2_ERR_OOM : H2_ERR_CUDA; \
+        }                                                        \
+    } while (0)
+
+namespace h2 {
+void set_last_error(const char* msg);
+}

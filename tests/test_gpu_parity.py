@@ -1,0 +1,164 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances: the FP64 path must match the oracle's H2 product to a relative
+L2 error of 1e-8 per right-hand side, the FP32 far-field path to 1e-5; the
+solid angles and the exact (all-near) operator agree to rounding (1e-12).
+The cluster tree and the block partition are index data and must be
+identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pkg = pytest.importorskip("paper_1811_05731_gb300")
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-8
+MIXED_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.build()
+    pkg.load()
+
+
+def rel_err(y, ref):
+    y = np.atleast_2d(y)
+    ref = np.atleast_2d(ref)
+    return np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+MESHES = {
+    "ico3": lambda: synth.icosphere(3),
+    "cube6": lambda: synth.cube_surface(6),
+    "ellipsoid2": lambda: synth.ellipsoid(2),
+    "box352": lambda: synth.box_surface(3, 5, 2, 1.0, 2.0, 0.3),
+    "cubesphere9": lambda: synth.cube_sphere(9),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MESHES))
+def test_psi_matches_oracle(name):
+    m = MESHES[name]()
+    g = pkg.Geometry(m.xyz, m.tri)
+    assert np.max(np.abs(g.psi() - oracle.psi(m.xyz, m.tri))) < 1e-12
+
+
+@pytest.mark.parametrize("mk,m_,leaf", [(lambda: synth.icosphere(3), 3, 32),
+                                        (lambda: synth.cube_surface(12), 4, 64),
+                                        (lambda: synth.box_surface(9, 4, 3, 3.0, 1.0, 0.5), 2, 8)])
+def test_tree_and_blocks_identical_to_oracle(mk, m_, leaf):
+    m = mk()
+    g = pkg.Geometry(m.xyz, m.tri)
+    op = pkg.Operator(g, m=m_, leaf=leaf)
+    o = oracle.H2Oracle(m.xyz, m.tri, m_, leaf, 2.0, store=False)
+    t, to = op.tree(), o.tree()
+    for key in ("perm", "start", "size", "parent", "child0", "child1", "level"):
+        assert np.array_equal(t[key], to[key]), key
+    assert np.array_equal(t["box"], to["box"])
+    b, bo = op.blocks(), o.blocks()
+    for kind in ("far", "near"):
+        got = set(zip(b[kind + "_t"].tolist(), b[kind + "_s"].tolist()))
+        want = set(zip(bo[kind + "_t"].tolist(), bo[kind + "_s"].tolist()))
+        assert got == want, kind
+    st = op.stats()
+    assert st["n_far_blocks"] == o.n_far and st["n_near_blocks"] == o.n_near
+    assert st["near_entries"] == o.near_entries
+
+
+CASES = [
+    # name, mesh, m, leaf, r
+    ("ico3_m3", lambda: synth.icosphere(3), 3, 32, 2),
+    ("cube12_m4", lambda: synth.cube_surface(12), 4, 64, 3),
+    ("ellipsoid3_m5", lambda: synth.ellipsoid(3), 5, 64, 1),
+    ("box_m2_leaf8", lambda: synth.box_surface(9, 4, 3, 3.0, 1.0, 0.5), 2, 8, 5),
+    ("cubesphere9_m4_leaf20", lambda: synth.cube_sphere(9), 4, 20, 17),
+]
+
+
+def _inputs(m, r, seed=7):
+    x = synth.gaussian_rhs(m.n_vertices, r, seed)
+    if r >= 2:
+        x[1] = 1.0
+    return x
+
+
+@pytest.mark.parametrize("name,mk,m_,leaf,r", CASES, ids=[c[0] for c in CASES])
+def test_fp64_matvec_matches_oracle(name, mk, m_, leaf, r):
+    m = mk()
+    x = _inputs(m, r)
+    g = pkg.Geometry(m.xyz, m.tri)
+    op = pkg.Operator(g, m=m_, leaf=leaf, max_rhs=max(r, 1))
+    y = op.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = oracle.H2Oracle(m.xyz, m.tri, m_, leaf, 2.0).matvec(x)
+    err = rel_err(y, ref)
+    assert np.all(err <= FP64_TOL), err
+
+
+@pytest.mark.parametrize("name,mk,m_,leaf,r", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_fp32_matvec_within_budget(name, mk, m_, leaf, r):
+    m = mk()
+    x = _inputs(m, r)
+    g = pkg.Geometry(m.xyz, m.tri)
+    op = pkg.Operator(g, m=m_, leaf=leaf, max_rhs=r, precision=pkg.FP32)
+    y = op.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = oracle.H2Oracle(m.xyz, m.tri, m_, leaf, 2.0).matvec(x)
+    err = rel_err(y, ref)
+    assert np.all(err <= MIXED_TOL), err
+
+
+def test_all_near_operator_is_the_dense_matrix():
+    # eta -> 0: nothing is admissible, every block is an exact near block
+    m = synth.icosphere(2)
+    g = pkg.Geometry(m.xyz, m.tri)
+    op = pkg.Operator(g, m=3, leaf=16, eta=1e-9, max_rhs=2)
+    assert op.stats()["n_far_blocks"] == 0
+    M = oracle.dense_matrix(m.xyz, m.tri)
+    x = np.vstack([synth.gaussian_rhs(m.n_vertices, 1, 3), np.ones((1, m.n_vertices))])
+    y = op.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert np.max(np.abs(y - x @ M.T)) < 1e-12
+    assert np.max(np.abs(y[1] + 1.0)) < 1e-12   # Gauss: M 1 = -1
+
+
+def test_host_pointer_path_matches_device_path():
+    m = synth.cube_surface(8)
+    x = synth.gaussian_rhs(m.n_vertices, 2, 5)
+    g = pkg.Geometry(m.xyz, m.tri)
+    op = pkg.Operator(g, m=3, leaf=24, max_rhs=2)
+    yd = op.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    yh = op.matvec(x)
+    assert np.max(np.abs(yd - yh)) <= 1e-14 * np.max(np.abs(yd))
+    assert pkg.h2_device_status(op.handle) == 0
+
+
+def test_rhs_limit_and_repeat_calls():
+    m = synth.icosphere(2)
+    g = pkg.Geometry(m.xyz, m.tri)
+    op = pkg.Operator(g, m=3, leaf=16, max_rhs=2)
+    x = torch.from_numpy(synth.gaussian_rhs(m.n_vertices, 3, 1)).cuda()
+    with pytest.raises(pkg.H2Error) as e:
+        op.matvec(x)
+    assert e.value.code == -8
+    a = op.matvec(x[:2].contiguous()).cpu().numpy()
+    b = op.matvec(x[:2].contiguous()).cpu().numpy()
+    c = op.matvec(x[:1].contiguous()).cpu().numpy()
+    assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(a))
+    assert np.max(np.abs(a[:1] - c)) <= 1e-14 * np.max(np.abs(a))
+
+
+def test_cube64_full_size_fp64():
+    """The benchmark configuration: unit cube, 64 x 64 per face, m = 4, leaf 64."""
+    w = synth.make_workload("cube64")
+    g = pkg.Geometry(w.mesh.xyz, w.mesh.tri)
+    op = pkg.Operator(g, m=w.m, leaf=w.leaf, eta=w.eta)
+    y = op.matvec(torch.from_numpy(w.u1).cuda()).cpu().numpy()
+    ref = oracle.H2Oracle(w.mesh.xyz, w.mesh.tri, w.m, w.leaf, w.eta).matvec(w.u1)
+    err = rel_err(y, ref)
+    assert np.all(err <= FP64_TOL), err
