@@ -49,7 +49,8 @@ typedef enum {
     H2_ERR_CUDA = -6,                 /* a CUDA runtime call failed */
     H2_ERR_TIMEOUT = -7,              /* a bounded device-side wait gave up */
     H2_ERR_RHS_EXCEEDS_MAX = -8,      /* r > h2_params.max_rhs */
-    H2_ERR_WRONG_HANDLE = -9          /* geometry given where an operator is needed, or vice versa */
+    H2_ERR_WRONG_HANDLE = -9,         /* geometry given where an operator is needed, or vice versa */
+    H2_ERR_SCRATCH_LIMIT = -10        /* h2_matvec_noalloc: problem larger than its fixed scratch */
 } h2_status;
 
 /* Storage/arithmetic precision of the far field (transfer, coupling and leaf
@@ -97,6 +98,23 @@ int h2_assemble(const h2_handle* geom, const h2_params* p, h2_handle** out_op);
  *           `cuda_stream` and returns after the result is in u2.
  *   1 <= r <= max_rhs.  u1 and u2 must not overlap.  u2 is overwritten. */
 int h2_matvec(h2_handle* op, const double* u1, double* u2, int32_t r, void* cuda_stream);
+
+/* u2 = M u1 like h2_matvec, for callers that cannot allocate device memory
+ * while they apply the operator (for example a time-stepping loop that
+ * reserved all device memory in advance, or an application whose device
+ * memory belongs to its own pool allocator).  The paper has no counterpart:
+ * this is a property of the library, not of the method.
+ *   u1, u2: DEVICE pointers only, r x N doubles as in h2_matvec; 1 <= r <= 32
+ *           (independent of max_rhs).  Asynchronous on `cuda_stream`.
+ * The workspace is a fixed array of 4,194,304 doubles (32 MiB) inside the
+ * library, present on every GPU that loads it until the process exits.
+ * Requires (N + 2 * n_clusters * k_even + 2) * r <= 4,194,304, else returns
+ * H2_ERR_SCRATCH_LIMIT without launching anything.  No cudaMalloc, cudaFree
+ * or other allocating routine is called.  The first call on a device looks up
+ * the array's device address (and loads the library's kernels on that
+ * device); make it before any stream capture.  Every call shares the array:
+ * calls whose executions overlap on the GPU race and give wrong results. */
+int h2_matvec_noalloc(h2_handle* op, const double* u1, double* u2, int32_t r, void* cuda_stream);
 
 /* Counts and sizes of an operator (Section "Results", "Data compression":
  * storage of the compressed operator and the compression ratio

@@ -75,13 +75,14 @@ def load(path: str | None = None):
                                         ctypes.POINTER(_vp)]
         L.h2_assemble.argtypes = [_vp, ctypes.POINTER(Params), ctypes.POINTER(_vp)]
         L.h2_matvec.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
+        L.h2_matvec_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
         L.h2_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
         L.h2_get_tree.argtypes = [_vp] + [_c_i32] * 7 + [_c_d]
         L.h2_get_blocks.argtypes = [_vp] + [_c_i32] * 4
         L.h2_get_psi.argtypes = [_vp, _c_d]
         L.h2_device_status.argtypes = [_vp]
         L.h2_free.argtypes = [_vp]
-        for f in ("h2_build_geometry", "h2_assemble", "h2_matvec", "h2_stats", "h2_get_tree",
+        for f in ("h2_build_geometry", "h2_assemble", "h2_matvec", "h2_matvec_noalloc", "h2_stats", "h2_get_tree",
                   "h2_get_blocks", "h2_get_psi", "h2_device_status", "h2_free"):
             getattr(L, f).restype = ctypes.c_int
         _LIB = L
@@ -141,6 +142,12 @@ def h2_matvec(op: int, u1_ptr: int, u2_ptr: int, r: int, stream=None) -> None:
     """u2 = M u1 on raw pointers (both device or both host), r x N row-major FP64."""
     _check(lib().h2_matvec(op, u1_ptr, u2_ptr, int(r), _stream_ptr(stream) if stream != 0 else 0),
            "h2_matvec")
+
+
+def h2_matvec_noalloc(op: int, u1_ptr: int, u2_ptr: int, r: int, stream=None) -> None:
+    """u2 = M u1 on device pointers with the library's fixed scratch (no device allocation)."""
+    _check(lib().h2_matvec_noalloc(op, u1_ptr, u2_ptr, int(r), _stream_ptr(stream)),
+           "h2_matvec_noalloc")
 
 
 def h2_stats(op: int) -> dict:

@@ -74,6 +74,7 @@ const char* h2_error_string(int code) {
         case H2_ERR_TIMEOUT: return "device-side wait timed out";
         case H2_ERR_RHS_EXCEEDS_MAX: return "number of right-hand sides exceeds max_rhs";
         case H2_ERR_WRONG_HANDLE: return "wrong handle kind";
+        case H2_ERR_SCRATCH_LIMIT: return "problem exceeds the fixed scratch of h2_matvec_noalloc";
         default: return "unknown status";
     }
 }

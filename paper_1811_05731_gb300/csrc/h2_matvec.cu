@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "h2_internal.h"
@@ -403,3 +404,108 @@ int matvec_device(h2_handle* op, const double* u1, double* u2, int r, cudaStream
 }
 
 }  // namespace h2
+
+// ---------------------------------------------------------------------------
+// h2_matvec_noalloc: the same product with a fixed, library-owned workspace.
+//
+// Some callers cannot allocate device memory when they apply the operator:
+// a time-stepping loop that reserved all of its device memory up front, an
+// application whose memory belongs to its own pool allocator, or code that
+// must not pay the device-wide synchronisation that cudaMalloc/cudaFree can
+// cause.  For them this variant takes its workspace (the permuted input and
+// the per-cluster x-hat / y-hat vectors) from the file-scope array below
+// instead of from the operator's own allocation.  It calls no allocating
+// CUDA or library routine.
+//
+// The array is H2_STATIC_WS_DOUBLES doubles (32 MiB) on every GPU that loads
+// this library, held until the process exits.  In host code its name is a
+// host-side stand-in, not a device address: the device address is obtained
+// once per device with cudaGetSymbolAddress (with that device current) on the
+// first call, which also makes the runtime load this module on that device.
+// Make that first call before any stream capture.  All calls share the one
+// array and it keeps the last call's contents; the gather kernel rewrites the
+// input rows and clears the accumulated y-hat rows on every call.  Calls whose
+// executions overlap on the GPU (different streams, different operators)
+// race on the array and give wrong results: serialise them.
+// ---------------------------------------------------------------------------
+#define H2_STATIC_WS_DOUBLES ((size_t)1 << 22)
+static __device__ __align__(256) double g_h2_static_ws[H2_STATIC_WS_DOUBLES];
+
+namespace h2 {
+namespace {
+constexpr int kMaxDevices = 64;
+double* g_static_ws_dev[kMaxDevices] = {nullptr};
+std::mutex g_static_ws_mu;
+
+int static_workspace(double** out) {
+    int dev = 0;
+    H2_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return H2_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_static_ws_mu);
+    if (!g_static_ws_dev[dev]) {
+        void* p = nullptr;
+        H2_CUDA_TRY(cudaGetSymbolAddress(&p, g_h2_static_ws));
+        g_static_ws_dev[dev] = static_cast<double*>(p);
+    }
+    *out = g_static_ws_dev[dev];
+    return H2_OK;
+}
+
+bool device_pointer(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+}  // namespace h2
+
+extern "C" int h2_matvec_noalloc(h2_handle* op, const double* u1, double* u2, int32_t r,
+                                 void* cuda_stream) {
+    using namespace h2;
+    if (!op || !u1 || !u2) return H2_ERR_INVALID_ARG;
+    if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
+    if (r < 1 || r > H2_MAX_RHS) return H2_ERR_INVALID_ARG;
+    const int64_t N = op->geom->N;
+    const size_t bytes = sizeof(double) * (size_t)N * r;
+    const char *a = (const char*)u1, *b = (const char*)u2;
+    if (a < b + bytes && b < a + bytes) return H2_ERR_INVALID_ARG;
+    if (!device_pointer(u1) || !device_pointer(u2)) return H2_ERR_INVALID_ARG;
+    if ((size_t)op->ws_rows * (size_t)r > H2_STATIC_WS_DOUBLES) {
+        set_last_error("h2_matvec_noalloc: workspace rows x r exceeds the fixed scratch of 4194304 doubles");
+        return H2_ERR_SCRATCH_LIMIT;
+    }
+    double* ws = nullptr;
+    int rc = static_workspace(&ws);
+    if (rc != H2_OK) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int rt = rt_for(r);
+    const size_t smem = pass_smem_bytes(op, rt);
+    {
+        const int64_t work = std::max<int64_t>(N * r, (int64_t)op->zero_rows.size() * op->kp * r);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 4096));
+        k_prologue<<<grid, 256, 0, s>>>(u1, ws, op->d_perm, N, r, op->d_zero_rows,
+                                        (int)op->zero_rows.size(), op->kp);
+        H2_CUDA_TRY(cudaGetLastError());
+    }
+    for (const Pass& p : op->passes) {
+        PassArgs pa{};
+        pa.seg = p.d_seg;
+        pa.chunk = p.d_chunk;
+        pa.piece = p.d_piece;
+        pa.arena = op->d_arena;
+        pa.ws = ws;
+        pa.u2 = u2;
+        pa.perm = op->d_perm;
+        pa.err = op->d_err;
+        pa.N = N;
+        pa.nseg = (int)p.seg.size();
+        pa.r = r;
+        pa.stages = op->stages;
+        pa.stage_bytes = op->stage_bytes;
+        H2_CUDA_TRY(launch_pass(pa, rt, p.grid, smem, s));
+    }
+    return H2_OK;
+}
