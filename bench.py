@@ -39,7 +39,7 @@ N_SM = 152
 FP64_FMA_PER_CLK_SM = 2
 FP32_FMA_PER_CLK_SM = 128
 PASS_NAMES = {0: "gather", 1: "up_leaf", 2: "up_transfer", 3: "coupling", 4: "down_transfer",
-              5: "leaf_near"}
+              5: "leaf_near", 6: "leaf_expand", 7: "flow"}
 
 WORKLOADS = {
     # name: (mesh builder, m, leaf, eta, r, rhs builder)
@@ -190,7 +190,8 @@ def run_gpu(args, rank, local, world):
     r = u1_np.shape[0]
     prec = pkg.FP32 if args.precision == "fp32" else pkg.FP64
     g = pkg.Geometry(mesh.xyz, mesh.tri)
-    op = pkg.Operator(g, m=m, leaf=leaf, eta=eta, precision=prec, max_rhs=r)
+    op = pkg.Operator(g, m=m, leaf=leaf, eta=eta, precision=prec, max_rhs=r,
+                      schedule=pkg.SCHEDULE_FLOW if args.schedule == "flow" else pkg.SCHEDULE_LEVELS)
     st = op.stats()
     stream = torch.cuda.current_stream()
     sp = int(stream.cuda_stream)
@@ -290,6 +291,9 @@ def run_gpu(args, rank, local, world):
         d["bytes"] += p["bytes"]
         d["macs"] += p["macs_per_rhs"]
         d["launches"] += 1
+    def kname(p):
+        return "k_flow (whole product)" if p["pass"] == "flow" else f"k_pass ({p['pass']})"
+
     if passes:
         dom = max((p for p in passes), key=lambda p: p["ms"])
         t = dom["ms"] / 1e3
@@ -305,11 +309,11 @@ def run_gpu(args, rank, local, world):
                         "peak_source": f"{'FP64' if prec == pkg.FP64 else 'FP32'} FMA rate: "
                                        f"{N_SM} SMs x {FP64_FMA_PER_CLK_SM if prec == pkg.FP64 else FP32_FMA_PER_CLK_SM}"
                                        f" FMA/clk x 2 x {sm_max:.0f} MHz",
-                        "kernel": f"k_pass ({dom['pass']})", "hbm_gbs": gbs, "hbm_frac_of_measured": hbm_frac}
+                        "kernel": kname(dom), "hbm_gbs": gbs, "hbm_frac_of_measured": hbm_frac}
         else:
             roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
                         "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
-                        "kernel": f"k_pass ({dom['pass']})", "alu_tflops": tfl, "alu_frac": alu_frac}
+                        "kernel": kname(dom), "alu_tflops": tfl, "alu_frac": alu_frac}
         tpath = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tpath):
             with open(tpath) as f:
@@ -334,6 +338,7 @@ def run_gpu(args, rank, local, world):
         "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "triangles": mesh.n_triangles, "m": m,
                    "leaf": leaf, "eta": eta, "r": r, "precision": args.precision,
+                   "schedule": args.schedule,
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2: {st['bytes_streamed'] / 1e6:.0f} MB of matrices "
                          f"streamed per step (L2 129 MB), no flush"},
@@ -362,6 +367,7 @@ def main():
     ap.add_argument("--workload", default="cube64", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--r", type=int, default=0)
+    ap.add_argument("--schedule", default="flow", choices=["flow", "levels"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

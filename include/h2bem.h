@@ -68,10 +68,19 @@ typedef struct {
     double box_inflation;   /* rho: every box side >= rho * longest side (0.25)       */
     int32_t precision;      /* h2_precision                                           */
     int32_t max_rhs;        /* largest r accepted by h2_matvec (workspace size), >= 1 */
-    int32_t reserved[4];    /* must be zero                                           */
+    int32_t schedule;       /* h2_schedule: how one h2_matvec is launched              */
+    int32_t reserved[3];    /* must be zero                                           */
 } h2_params;
 
-/* Fills `p` with the defaults: m = 4, leaf = 64, eta = 2, rho = 0.25, FP64, max_rhs = 1. */
+/* H2_SCHEDULE_FLOW (default): one persistent kernel after the input gather;
+ *   its CTAs take the product's segments in a dependency order and wait
+ *   (bounded) for the cluster vectors they read.
+ * H2_SCHEDULE_LEVELS: one kernel per pass (upward leaf projection, each
+ *   upward level, coupling, each downward level, near field, leaf expansion). */
+typedef enum { H2_SCHEDULE_FLOW = 0, H2_SCHEDULE_LEVELS = 1 } h2_schedule;
+
+/* Fills `p` with the defaults: m = 4, leaf = 64, eta = 2, rho = 0.25, FP64, max_rhs = 1,
+ * flow schedule. */
 void h2_default_params(h2_params* p);
 
 /* Build a geometry handle from a closed, outward-oriented triangle mesh
@@ -167,8 +176,9 @@ int h2_profile_enable(h2_handle* op, int32_t enable);
 
 /* Synchronises on the recorded events and returns, per launch of one
  * h2_matvec in launch order (entry 0 = the input gather, then one entry per
- * pass), the pass kind (0 gather, 1 upward leaf projection, 2 upward
- * transfer, 3 coupling, 4 downward transfer, 5 leaf expansion + near field),
+ * pass, or one entry for the single flow kernel), the pass kind (0 gather,
+ * 1 upward leaf projection, 2 upward transfer, 3 coupling, 4 downward
+ * transfer, 5 near field, 6 leaf expansion, 7 the whole flow kernel),
  * the total milliseconds over all recorded calls, the matrix bytes and the
  * multiply-adds (per right-hand side) of one launch, and its grid size.
  * Arrays hold `capacity` entries (any may be NULL); *n_entries is the number

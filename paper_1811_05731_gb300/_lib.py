@@ -11,6 +11,8 @@ from .build import lib_path
 
 FP64 = 0
 FP32 = 1
+SCHEDULE_FLOW = 0
+SCHEDULE_LEVELS = 1
 
 _LIB = None
 _LOCK = threading.Lock()
@@ -35,7 +37,8 @@ class H2Error(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("leaf", ctypes.c_int32), ("eta", ctypes.c_double),
                 ("box_inflation", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("max_rhs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("max_rhs", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -225,11 +228,12 @@ class Operator:
     """H2 approximation of M = K + D on one GPU."""
 
     def __init__(self, geom: Geometry, m: int = 4, leaf: int = 64, eta: float = 2.0,
-                 rho: float = 0.25, precision: int = FP64, max_rhs: int = 1):
+                 rho: float = 0.25, precision: int = FP64, max_rhs: int = 1,
+                 schedule: int = SCHEDULE_FLOW):
         self.geom = geom
         self.N = geom.N
         self.params = h2_default_params(m=m, leaf=leaf, eta=eta, box_inflation=rho,
-                                        precision=precision, max_rhs=max_rhs)
+                                        precision=precision, max_rhs=max_rhs, schedule=schedule)
         self.handle = h2_assemble(geom.handle, self.params)
 
     def stats(self) -> dict:

@@ -26,6 +26,8 @@ void free_device(h2_handle* h) {
         h2::release_profile(h);
         for (h2::Pass& p : h->passes) { f(p.d_seg); f(p.d_chunk); f(p.d_piece); }
         f(h->d_arena); f(h->d_perm); f(h->d_box); f(h->d_ws); f(h->d_zero_rows); f(h->d_io); f(h->d_err);
+        f(h->d_fseg); f(h->d_fchunk); f(h->d_fpiece); f(h->d_fdeps); f(h->d_fexpect); f(h->d_fzero_rows);
+        f(h->d_fcnt);
     }
 }
 
@@ -60,6 +62,7 @@ void h2_default_params(h2_params* p) {
     p->box_inflation = 0.25;
     p->precision = H2_FP64;
     p->max_rhs = 1;
+    p->schedule = H2_SCHEDULE_FLOW;
 }
 
 const char* h2_error_string(int code) {
@@ -117,9 +120,10 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
     else h2_default_params(&p);
     if (p.m < 1 || p.m > H2_MAX_M || p.leaf < 1 || p.leaf > H2_MAX_LEAF || !(p.eta > 0.0) ||
         !(p.box_inflation > 0.0) || p.box_inflation > 1.0 || p.max_rhs < 1 || p.max_rhs > H2_MAX_RHS ||
-        (p.precision != H2_FP64 && p.precision != H2_FP32))
+        (p.precision != H2_FP64 && p.precision != H2_FP32) ||
+        (p.schedule != H2_SCHEDULE_FLOW && p.schedule != H2_SCHEDULE_LEVELS))
         return H2_ERR_INVALID_ARG;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
         if (p.reserved[i] != 0) return H2_ERR_INVALID_ARG;
     const auto t0 = std::chrono::steady_clock::now();
     h2_handle* geom = const_cast<h2_handle*>(geom_c);
@@ -136,6 +140,7 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
     h2::build_cluster_tree(op);
     h2::build_block_partition(op);
     h2::build_plan(op);
+    if (p.schedule == H2_SCHEDULE_FLOW) h2::build_flow(op);
     int rc = h2::upload_plan(op);
     if (rc == H2_OK) rc = h2::assemble_device(op, nullptr);
     if (rc != H2_OK) {
@@ -210,13 +215,25 @@ int h2_profile_read(h2_handle* op, int32_t capacity, int32_t* kind, double* ms_t
     *n_calls = n;
     *n_entries = (int32_t)ms.size();
     for (int32_t i = 0; i < (int32_t)ms.size() && i < capacity; ++i) {
-        const bool pro = i == 0;
-        const h2::Pass* p = pro ? nullptr : &op->passes[(size_t)i - 1];
-        if (kind) kind[i] = pro ? h2::PASS_PROLOGUE : p->kind;
+        int32_t kd = h2::PASS_PROLOGUE, gr = 0;
+        int64_t by = 0, mc = 0;
+        if (i > 0 && op->use_flow) {
+            kd = h2::PASS_FLOW;
+            by = op->bytes_streamed;
+            mc = op->macs;
+            gr = op->flow_grid;
+        } else if (i > 0) {
+            const h2::Pass& p = op->passes[(size_t)i - 1];
+            kd = p.kind;
+            by = p.bytes;
+            mc = p.macs;
+            gr = p.grid;
+        }
+        if (kind) kind[i] = kd;
         if (ms_total) ms_total[i] = ms[(size_t)i];
-        if (bytes) bytes[i] = pro ? 0 : p->bytes;
-        if (macs) macs[i] = pro ? 0 : p->macs;
-        if (grid) grid[i] = pro ? 0 : p->grid;
+        if (bytes) bytes[i] = by;
+        if (macs) macs[i] = mc;
+        if (grid) grid[i] = gr;
     }
     return H2_OK;
 }

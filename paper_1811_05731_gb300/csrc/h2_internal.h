@@ -24,6 +24,7 @@
 #define H2_MAX_K 125
 #define H2_MAX_LEAF 128
 #define H2_MAX_RHS 32
+#define H2_MAX_CHUNK_COLS 128   // input columns of one chunk (shared-memory staging)
 
 namespace h2 {
 
@@ -32,6 +33,7 @@ enum SegMode : int32_t {
     SEG_ATOMIC = 1,     // atomicAdd(ws[out_row + i], sum)
     SEG_FINAL = 2,      // u2[c * N + perm[out_row + i]] = sum
     SEG_ADD = 3,        // ws[out_row + i] += sum (single writer per pass)
+    SEG_FINAL_ADD = 4,  // u2[c * N + perm[out_row + i]] += sum (after the near field)
 };
 
 enum PieceType : int32_t { PIECE_F64 = 0, PIECE_F32 = 1 };
@@ -68,7 +70,7 @@ struct Segment {
 // Host plan of one pass plus its device copies.
 enum PassKind : int32_t {
     PASS_PROLOGUE = 0, PASS_UP_LEAF = 1, PASS_UP_TRANSFER = 2, PASS_COUPLING = 3,
-    PASS_DOWN_TRANSFER = 4, PASS_LEAF_NEAR = 5,
+    PASS_DOWN_TRANSFER = 4, PASS_LEAF_NEAR = 5, PASS_LEAF_EXPAND = 6, PASS_FLOW = 7,
 };
 
 struct Pass {
@@ -83,6 +85,19 @@ struct Pass {
     int64_t bytes = 0;        // arena bytes streamed by the pass
     int64_t macs = 0;         // multiply-adds per right-hand side
     int grid = 0;
+};
+
+// One segment of the single-launch dataflow form of the product.  Segments
+// are stored in ticket order (a topological order of their dependencies);
+// a segment waits until each region in deps[dep0 .. dep0+ndep) has reached
+// its expected producer count, and increments `signal` when its output is
+// written.  Regions: x-hat of cluster c = c, y-hat of c = nc + c, u2 rows of
+// leaf t = 2 nc + t.
+struct FlowSeg {
+    Segment s;           // chunk0 indexes the flow chunk array
+    int32_t signal;      // region completed by this segment (-1: none)
+    int32_t dep0, ndep;
+    int32_t kind;        // PassKind of the originating pass
 };
 
 // Where one matrix lives in the arena.
@@ -140,7 +155,7 @@ struct h2_handle {
     int64_t bytes_streamed = 0, macs = 0;
     int64_t far_bytes = 0, near_bytes = 0, basis_coefficients = 0, near_entries = 0;
     double assemble_seconds = 0.0;
-    int stages = 4;                   // shared-memory stages of the pass kernel
+    int stages = 3;                   // shared-memory stages of the pass kernel
     int stage_bytes = 32768;
     // CUDA graph of one matvec (rebuilt when r changes)
     cudaGraph_t graph = nullptr;
@@ -150,6 +165,20 @@ struct h2_handle {
     double* graph_u2 = nullptr;
     cudaGraphNode_t node_first = nullptr, node_last = nullptr;
     int n_launches = 0;
+    // single-launch dataflow form
+    std::vector<h2::FlowSeg> fseg;
+    std::vector<h2::Chunk> fchunk;
+    std::vector<h2::Piece> fpiece;
+    std::vector<int32_t> fdeps, fexpect, fzero_rows;
+    h2::FlowSeg* d_fseg = nullptr;
+    h2::Chunk* d_fchunk = nullptr;
+    h2::Piece* d_fpiece = nullptr;
+    int32_t* d_fdeps = nullptr;
+    int32_t* d_fexpect = nullptr;
+    int32_t* d_fzero_rows = nullptr;
+    int32_t* d_fcnt = nullptr;        // 3 nc region counters + 1 ticket counter
+    int flow_grid = 0;
+    int use_flow = 1;
     // per-pass timing with CUDA events (profiling aid, off by default)
     int prof_enabled = 0;
     std::vector<std::vector<cudaEvent_t>> prof_calls;   // events of each profiled call
@@ -164,6 +193,7 @@ void build_cluster_tree(h2_handle* op);
 void build_block_partition(h2_handle* op);
 void gauss_legendre_unit(int q, std::vector<double>& x, std::vector<double>& w);
 void build_plan(h2_handle* op);   // arena layout + passes (h2_plan.cpp)
+void build_flow(h2_handle* op);   // single-launch dataflow order (h2_plan.cpp)
 
 // device-side assembly and matvec (h2_assemble.cu, h2_matvec.cu)
 int geometry_device_setup(h2_handle* g, cudaStream_t s);

@@ -90,24 +90,29 @@ def _inputs(m, r, seed=7):
     return x
 
 
+SCHEDULES = {"flow": 0, "levels": 1}
+
+
+@pytest.mark.parametrize("schedule", sorted(SCHEDULES))
 @pytest.mark.parametrize("name,mk,m_,leaf,r", CASES, ids=[c[0] for c in CASES])
-def test_fp64_matvec_matches_oracle(name, mk, m_, leaf, r):
+def test_fp64_matvec_matches_oracle(name, mk, m_, leaf, r, schedule):
     m = mk()
     x = _inputs(m, r)
     g = pkg.Geometry(m.xyz, m.tri)
-    op = pkg.Operator(g, m=m_, leaf=leaf, max_rhs=max(r, 1))
+    op = pkg.Operator(g, m=m_, leaf=leaf, max_rhs=max(r, 1), schedule=SCHEDULES[schedule])
     y = op.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
     ref = oracle.H2Oracle(m.xyz, m.tri, m_, leaf, 2.0).matvec(x)
     err = rel_err(y, ref)
     assert np.all(err <= FP64_TOL), err
 
 
+@pytest.mark.parametrize("schedule", sorted(SCHEDULES))
 @pytest.mark.parametrize("name,mk,m_,leaf,r", CASES[:3], ids=[c[0] for c in CASES[:3]])
-def test_fp32_matvec_within_budget(name, mk, m_, leaf, r):
+def test_fp32_matvec_within_budget(name, mk, m_, leaf, r, schedule):
     m = mk()
     x = _inputs(m, r)
     g = pkg.Geometry(m.xyz, m.tri)
-    op = pkg.Operator(g, m=m_, leaf=leaf, max_rhs=r, precision=pkg.FP32)
+    op = pkg.Operator(g, m=m_, leaf=leaf, max_rhs=r, precision=pkg.FP32, schedule=SCHEDULES[schedule])
     y = op.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
     ref = oracle.H2Oracle(m.xyz, m.tri, m_, leaf, 2.0).matvec(x)
     err = rel_err(y, ref)
@@ -153,12 +158,32 @@ def test_rhs_limit_and_repeat_calls():
     assert np.max(np.abs(a[:1] - c)) <= 1e-14 * np.max(np.abs(a))
 
 
-def test_cube64_full_size_fp64():
-    """The benchmark configuration: unit cube, 64 x 64 per face, m = 4, leaf 64."""
+@pytest.fixture(scope="module")
+def cube64_ref():
     w = synth.make_workload("cube64")
-    g = pkg.Geometry(w.mesh.xyz, w.mesh.tri)
-    op = pkg.Operator(g, m=w.m, leaf=w.leaf, eta=w.eta)
-    y = op.matvec(torch.from_numpy(w.u1).cuda()).cpu().numpy()
     ref = oracle.H2Oracle(w.mesh.xyz, w.mesh.tri, w.m, w.leaf, w.eta).matvec(w.u1)
-    err = rel_err(y, ref)
-    assert np.all(err <= FP64_TOL), err
+    return w, ref
+
+
+@pytest.mark.parametrize("schedule", sorted(SCHEDULES))
+def test_cube64_full_size_fp64(cube64_ref, schedule):
+    """The benchmark configuration: unit cube, 64 x 64 per face, m = 4, leaf 64."""
+    w, ref = cube64_ref
+    g = pkg.Geometry(w.mesh.xyz, w.mesh.tri)
+    op = pkg.Operator(g, m=w.m, leaf=w.leaf, eta=w.eta, schedule=SCHEDULES[schedule])
+    x = torch.from_numpy(w.u1).cuda()
+    for _ in range(3):   # repeated calls reuse the counters and the workspace
+        y = op.matvec(x).cpu().numpy()
+        err = rel_err(y, ref)
+        assert np.all(err <= FP64_TOL), err
+    assert pkg.h2_device_status(op.handle) == 0
+    st = op.stats()
+    assert st["n_launches_matvec"] == (2 if schedule == "flow" else 1 + st["n_passes"])
+
+
+def test_cube64_full_size_fp32(cube64_ref):
+    w, ref = cube64_ref
+    g = pkg.Geometry(w.mesh.xyz, w.mesh.tri)
+    op = pkg.Operator(g, m=w.m, leaf=w.leaf, eta=w.eta, precision=pkg.FP32)
+    y = op.matvec(torch.from_numpy(w.u1).cuda()).cpu().numpy()
+    assert np.all(rel_err(y, ref) <= MIXED_TOL)
