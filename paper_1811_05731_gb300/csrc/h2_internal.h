@@ -178,7 +178,7 @@ struct h2_handle {
     int32_t* d_fzero_rows = nullptr;
     int32_t* d_fcnt = nullptr;        // 3 nc region counters + 1 ticket counter
     int flow_grid = 0;
-    int use_flow = 1;
+    int use_flow = 0;
     // per-pass timing with CUDA events (profiling aid, off by default)
     int prof_enabled = 0;
     std::vector<std::vector<cudaEvent_t>> prof_calls;   // events of each profiled call

@@ -367,6 +367,17 @@ struct FlowCursor {
     }
 };
 
+#ifdef H2_TRACE
+// Per-segment timeline (diagnostic builds only): ticket, SM, start, inputs
+// ready, end (globaltimer ns).
+__device__ long long g_h2_trace[1 << 22];
+__device__ __forceinline__ unsigned smid() {
+    unsigned v;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(v));
+    return v;
+}
+#endif
+
 template <int RT>
 __global__ void __launch_bounds__(kThreads, 1) k_flow(const FlowArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -402,6 +413,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_flow(const FlowArgs a) {
         if (sg < 0) break;
         const FlowSeg F = a.seg[sg];
         const Segment S = F.s;
+#ifdef H2_TRACE
+        long long tr0 = (long long)now_ns();
+#endif
         // wait until every region this segment reads is complete
         if (tid == 0) {
             for (int d = F.dep0; d < F.dep0 + F.ndep && !abort_flag; ++d) {
@@ -420,6 +434,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_flow(const FlowArgs a) {
         }
         __syncthreads();
         if (abort_flag) goto bail;
+#ifdef H2_TRACE
+        long long tr1 = (long long)now_ns();
+#endif
 
         const int nrows = S.nrows;
         const int G = kThreads / nrows;
@@ -461,6 +478,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_flow(const FlowArgs a) {
         __threadfence();
         __syncthreads();
         if (tid == 0 && F.signal >= 0) atomicAdd(a.cnt + F.signal, 1);
+#ifdef H2_TRACE
+        if (tid == 0 && 5 * (sg + 1) < (1 << 22)) {
+            long long* t = g_h2_trace + 5 * sg;
+            t[0] = sg; t[1] = (long long)F.kind * 1000000 + smid() * 1000 + blockIdx.x % 1000; t[2] = tr0; t[3] = tr1;
+            t[4] = (long long)now_ns();
+        }
+#endif
     }
     return;
 
@@ -809,3 +833,13 @@ extern "C" int h2_matvec_noalloc(h2_handle* op, const double* u1, double* u2, in
     if (rc != H2_OK) return rc;
     return launch_matvec(op, u1, u2, r, (cudaStream_t)cuda_stream, ws, false, nullptr, nullptr);
 }
+
+#ifdef H2_TRACE
+// Copies the first n segment records of the last traced flow launch to host.
+extern "C" int h2_trace_read(long long* out, int n) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return H2_ERR_CUDA;
+    if (cudaMemcpyFromSymbol(out, h2::g_h2_trace, sizeof(long long) * 5 * (size_t)n) != cudaSuccess)
+        return H2_ERR_CUDA;
+    return H2_OK;
+}
+#endif
