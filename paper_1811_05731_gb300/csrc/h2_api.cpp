@@ -140,8 +140,13 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
     h2::build_cluster_tree(op);
     h2::build_block_partition(op);
     h2::build_plan(op);
-    if (p.schedule == H2_SCHEDULE_FLOW) h2::build_flow(op);
-    int rc = h2::upload_plan(op);
+    int rc = H2_OK;
+    if (p.schedule == H2_SCHEDULE_FLOW) {
+        h2::FlowModel fm;
+        rc = h2::flow_model(op, fm);
+        if (rc == H2_OK) op->flow_makespan_us = h2::build_flow(op, fm);
+    }
+    if (rc == H2_OK) rc = h2::upload_plan(op);
     if (rc == H2_OK) rc = h2::assemble_device(op, nullptr);
     if (rc != H2_OK) {
         release(op);

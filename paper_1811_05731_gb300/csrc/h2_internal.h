@@ -46,7 +46,7 @@ struct Chunk {
     int32_t bytes;       // multiple of 16
     int32_t piece0;      // first piece (index into the pass's piece array)
     int32_t npieces;
-    int32_t pad;
+    int32_t ncols;       // input columns of all its pieces (<= H2_MAX_CHUNK_COLS)
 };
 
 // One column-major matrix (nrows x ncols, nrows = the segment's) inside a
@@ -73,18 +73,20 @@ enum PassKind : int32_t {
     PASS_DOWN_TRANSFER = 4, PASS_LEAF_NEAR = 5, PASS_LEAF_EXPAND = 6, PASS_FLOW = 7,
 };
 
+struct FlowSeg;
+
 struct Pass {
     std::string name;
     int32_t kind = 0;
     std::vector<Segment> seg;
     std::vector<Chunk> chunk;
     std::vector<Piece> piece;
-    Segment* d_seg = nullptr;
+    FlowSeg* d_seg = nullptr;           // uploaded as segments without dependencies
     Chunk* d_chunk = nullptr;
     Piece* d_piece = nullptr;
     int64_t bytes = 0;        // arena bytes streamed by the pass
     int64_t macs = 0;         // multiply-adds per right-hand side
-    int grid = 0;
+    int grid = 0;             // CTAs of the last launch
 };
 
 // One segment of the single-launch dataflow form of the product.  Segments
@@ -157,6 +159,8 @@ struct h2_handle {
     double assemble_seconds = 0.0;
     int stages = 3;                   // shared-memory stages of the pass kernel
     int stage_bytes = 32768;
+    int coupling_split = 4;           // far blocks per coupling segment
+    double flow_makespan_us = 0.0;    // simulated duration of the dataflow order
     // CUDA graph of one matvec (rebuilt when r changes)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -177,7 +181,8 @@ struct h2_handle {
     int32_t* d_fexpect = nullptr;
     int32_t* d_fzero_rows = nullptr;
     int32_t* d_fcnt = nullptr;        // 3 nc region counters + 1 ticket counter
-    int flow_grid = 0;
+    int flow_grid = 0;                // CTAs of the last dataflow launch
+    int nsm = 0;                      // SMs of the device
     int use_flow = 0;
     // per-pass timing with CUDA events (profiling aid, off by default)
     int prof_enabled = 0;
@@ -186,6 +191,18 @@ struct h2_handle {
 };
 
 namespace h2 {
+// Cost model of one CTA of the segment kernel, used to order the dataflow
+// form (list scheduling on `workers` simulated CTAs).
+struct FlowModel {
+    int workers = 304;           // resident CTAs of the launch
+    int r = 1;                   // right-hand sides the order is tuned for
+    double seg_ns = 1500.0;      // fixed cost of a segment (dependency signal, reduction, write)
+    double chunk_ns = 150.0;     // fixed cost of a chunk (barrier, input staging)
+    double f64_per_ns = 2.07;    // FP64 multiply-adds per ns of one CTA
+    double f32_per_ns = 130.0;   // FP32 multiply-adds per ns of one CTA
+    double bytes_per_ns = 22.0;  // HBM bytes per ns of one CTA
+};
+
 // host-side builders (h2_host.cpp)
 int validate_mesh(const double* xyz, int64_t N, const int32_t* tri, int64_t T,
                   std::vector<int64_t>& adj_ptr, std::vector<int32_t>& adj);
@@ -193,7 +210,7 @@ void build_cluster_tree(h2_handle* op);
 void build_block_partition(h2_handle* op);
 void gauss_legendre_unit(int q, std::vector<double>& x, std::vector<double>& w);
 void build_plan(h2_handle* op);   // arena layout + passes (h2_plan.cpp)
-void build_flow(h2_handle* op);   // single-launch dataflow order (h2_plan.cpp)
+double build_flow(h2_handle* op, const FlowModel& fm);   // dataflow order (h2_plan.cpp)
 
 // device-side assembly and matvec (h2_assemble.cu, h2_matvec.cu)
 int geometry_device_setup(h2_handle* g, cudaStream_t s);
@@ -204,6 +221,7 @@ void release_graph(h2_handle* op);
 void release_profile(h2_handle* op);
 int read_profile(h2_handle* op, std::vector<double>& ms, int& ncalls);
 size_t pass_smem_bytes(const h2_handle* op, int rt);
+int flow_model(h2_handle* op, FlowModel& fm);   // CTAs and rates of the device
 }  // namespace h2
 
 #define H2_CUDA_TRY(call)                                        \

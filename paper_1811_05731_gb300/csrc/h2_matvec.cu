@@ -38,8 +38,9 @@ namespace h2 {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kQueue = 16;                               // segment queue of the flow kernel
+constexpr int kConsumers = 256;                          // compute threads (8 warps)
+constexpr int kBlock = kConsumers + 32;                  // + one producer warp
+constexpr int kMaxStages = 4;
 constexpr int kMaxChunkCols = H2_MAX_CHUNK_COLS;         // input columns staged per chunk
 constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s bound on every device-side wait
 
@@ -91,49 +92,149 @@ __device__ __forceinline__ int ld_acquire(const int32_t* p) {
     return v;
 }
 
-// Copies the input slices of the pieces of one chunk into shared memory
-// (FP64, or FP32 for FP32 pieces): one L2 read per value instead of one per
-// thread and column.  Inputs are read through L2 (ld.global.cg): in the flow
-// kernel they are written by other CTAs of the same launch.
+// What the producer warp publishes with every staged chunk.
+struct StageDesc {
+    int32_t seg;       // segment index (-1: this CTA has no more work)
+    int32_t last;      // 1 if the chunk is the last of its segment
+    int32_t piece0, npieces;
+    int32_t out_row, nrows, mode, signal;
+};
+
+struct KArgs {
+    const FlowSeg* seg;        // segments (dataflow form: in ticket order)
+    const Chunk* chunk;
+    const Piece* piece;
+    const int32_t* deps;       // dataflow form only
+    const int32_t* expect;     // dataflow form only
+    int32_t* cnt;              // dataflow form: region counters, ticket counter at [nreg]
+    const unsigned char* arena;
+    double* ws;
+    double* u2;
+    const int32_t* perm;
+    int* err;
+    int64_t N;
+    int nseg;
+    int nreg;
+    int r;
+    int stages;
+    int stage_bytes;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// Bounded wait that also gives up as soon as another thread of the CTA set
+// the abort flag.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    while (true) {
+        for (int i = 0; i < 16; ++i)
+            if (mbar_try(bar, parity)) return true;
+        if (*abort_flag || now_ns() - t0 > kWaitNs) return false;
+    }
+}
+__device__ __forceinline__ void signal_region(int32_t* p) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(p) : "memory");
+}
+
+// The producer warp's cursor over the chunks of its CTA (lane 0).
+// FLOW: segments come from the global ticket counter (topological order);
+// otherwise segments blockIdx.x, blockIdx.x + gridDim.x, ... of one pass.
+template <bool FLOW>
+struct Cursor {
+    int seg = -1, ci = 0, nchunks = 0, k = 0, done = 0;
+    __device__ void next(const KArgs& a, int& out_seg, int& out_ci) {
+        out_seg = -1;
+        out_ci = 0;
+        while (!done) {
+            if (seg >= 0 && ci < nchunks) {
+                out_seg = seg;
+                out_ci = ci++;
+                return;
+            }
+            int t;
+            if (FLOW) t = atomicAdd(a.cnt + a.nreg, 1);
+            else t = (int)blockIdx.x + (k++) * (int)gridDim.x;
+            if (t >= a.nseg) {
+                done = 1;
+                return;
+            }
+            seg = t;
+            ci = 0;
+            nchunks = a.seg[t].s.nchunks;
+        }
+    }
+};
+
+// Bounded wait (lane 0 of the producer) until every region segment `sg`
+// reads has all its producers done.  False on timeout or abort.
+__device__ bool deps_wait(const KArgs& a, int sg, volatile int* abort_flag) {
+    const FlowSeg& F = a.seg[sg];
+    for (int d = F.dep0; d < F.dep0 + F.ndep; ++d) {
+        const int reg = a.deps[d];
+        const int want = a.expect[reg];
+        if (ld_acquire(a.cnt + reg) >= want) continue;
+        const unsigned long long t0 = now_ns();
+        while (ld_acquire(a.cnt + reg) < want) {
+            if (*abort_flag || ld_acquire(a.err) != 0 || now_ns() - t0 > kWaitNs) return false;
+            __nanosleep(32);
+        }
+    }
+    return true;
+}
+
+// The producer warp copies the input values of chunk C (the workspace rows of
+// its pieces, concatenated, r values per row) into a stage's input buffer
+// laid out [column of the chunk][RT], FP64 or (FP32 chunks) FP32.  Inputs are
+// read through L2 (ld.global.cg): in the dataflow form other CTAs of the same
+// launch wrote them.
 template <int RT>
-__device__ __forceinline__ void stage_inputs(const Chunk& C, const Piece* __restrict__ pieces,
-                                             const double* __restrict__ ws, int r, unsigned char* xin) {
-    int off = 0;   // bytes
-    for (int p = C.piece0; p < C.piece0 + C.npieces; ++p) {
-        const Piece P = pieces[p];
-        const double* __restrict__ in = ws + (int64_t)P.in_row * r;
-        const int n = P.ncols * r;
-        if (P.type == PIECE_F64) {
-            double* x = reinterpret_cast<double*>(xin + off);
-            for (int idx = threadIdx.x; idx < n; idx += kThreads) {
-                const int j = idx / r, c = idx - j * r;
-                x[j * RT + c] = __ldcg(in + idx);
+__device__ __forceinline__ void stage_inputs(const KArgs& a, const Chunk& C, unsigned char* xin, int lane) {
+    constexpr int B = 8;   // loads in flight per lane
+    const int r = a.r;
+    const int total = C.ncols * r;
+    const bool f32 = a.piece[C.piece0].type == PIECE_F32;
+    int p = C.piece0, col0 = 0;
+    Piece P = a.piece[p];
+    for (int base = 0; base < total; base += 32 * B) {
+        double v[B];
+        int dst[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int idx = base + lane + 32 * j;
+            dst[j] = -1;
+            if (idx < total) {
+                const int col = idx / r, cc = idx - col * r;
+                while (col >= col0 + P.ncols) {
+                    col0 += P.ncols;
+                    P = a.piece[++p];
+                }
+                v[j] = __ldcg(a.ws + (int64_t)(P.in_row + col - col0) * r + cc);
+                dst[j] = col * RT + cc;
             }
-            off += P.ncols * RT * 8;
-        } else {
-            float* x = reinterpret_cast<float*>(xin + off);
-            for (int idx = threadIdx.x; idx < n; idx += kThreads) {
-                const int j = idx / r, c = idx - j * r;
-                x[j * RT + c] = (float)__ldcg(in + idx);
-            }
-            off += ((P.ncols * RT * 4 + 15) & ~15);
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            if (dst[j] < 0) continue;
+            if (f32) reinterpret_cast<float*>(xin)[dst[j]] = (float)v[j];
+            else reinterpret_cast<double*>(xin)[dst[j]] = v[j];
         }
     }
 }
 
 // Multiplies the pieces of one staged chunk into the thread's accumulators.
 template <int RT>
-__device__ __forceinline__ void consume_chunk(const unsigned char* stage, const Chunk& C,
+__device__ __forceinline__ void consume_chunk(const unsigned char* stage, int piece0, int npieces,
                                               const Piece* __restrict__ pieces, const unsigned char* xin,
                                               int r, int nrows, int row, int g, int G, double (&acc)[RT]) {
-    int off = 0;
-    for (int p = C.piece0; p < C.piece0 + C.npieces; ++p) {
+    int xcol = 0;
+    for (int p = piece0; p < piece0 + npieces; ++p) {
         const Piece P = pieces[p];
         const int nc = P.ncols;
         if (P.type == PIECE_F64) {
             const double* A = reinterpret_cast<const double*>(stage + P.smem_off) + row;
-            const double* x = reinterpret_cast<const double*>(xin + off);
-            off += nc * RT * 8;
+            const double* x = reinterpret_cast<const double*>(xin) + xcol * RT;
             if (RT == 1) {
                 double a0 = 0.0, a1 = 0.0;
                 int col = g;
@@ -155,8 +256,7 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const 
             }
         } else {
             const float* A = reinterpret_cast<const float*>(stage + P.smem_off) + row;
-            const float* x = reinterpret_cast<const float*>(xin + off);
-            off += ((nc * RT * 4 + 15) & ~15);
+            const float* x = reinterpret_cast<const float*>(xin) + xcol * RT;
             if (RT == 1) {
                 float a0 = 0.0f, a1 = 0.0f;
                 int col = g;
@@ -166,7 +266,7 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const 
                     a1 = fmaf(A[(col + G) * nrows], x[col + G], a1);
                 }
                 if (col < nc) a0 = fmaf(A[col * nrows], x[col], a0);
-                acc[0] += (double)a0 + (double)a1;
+                acc[0] += (double)(a0 + a1);
             } else {
                 float acc32[RT];
 #pragma unroll
@@ -182,321 +282,188 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const 
                 for (int c = 0; c < RT; ++c) acc[c] += (double)acc32[c];
             }
         }
+        xcol += nc;
     }
 }
 
-// Adds the G partial sums of every row and writes the segment.
+// Adds the G partial sums of every row and writes the segment (consumer threads).
 template <int RT>
-__device__ __forceinline__ void write_segment(const Segment& S, int mode, const double* red, int r,
-                                              int G, double* ws, double* u2,
-                                              const int32_t* __restrict__ perm, int64_t N) {
-    const int nrows = S.nrows;
-    for (int idx = threadIdx.x; idx < nrows * r; idx += kThreads) {
+__device__ __forceinline__ void write_segment(const StageDesc& D, const double* red, int r, int G,
+                                              double* ws, double* u2, const int32_t* __restrict__ perm,
+                                              int64_t N) {
+    const int nrows = D.nrows;
+    for (int idx = threadIdx.x; idx < nrows * r; idx += kConsumers) {
         const int rr = idx / r, c = idx - rr * r;
         double s = 0.0;
         for (int g2 = 0; g2 < G; ++g2) s += red[(g2 * nrows + rr) * RT + c];
-        if (mode == SEG_FINAL || mode == SEG_FINAL_ADD) {
-            double* dst = u2 + (int64_t)c * N + perm[S.out_row + rr];
-            if (mode == SEG_FINAL) *dst = s;
+        if (D.mode == SEG_FINAL || D.mode == SEG_FINAL_ADD) {
+            double* dst = u2 + (int64_t)c * N + perm[D.out_row + rr];
+            if (D.mode == SEG_FINAL) *dst = s;
             else *dst = __ldcg(dst) + s;
         } else {
-            double* dst = ws + (int64_t)(S.out_row + rr) * r + c;
-            if (mode == SEG_STORE) *dst = s;
-            else if (mode == SEG_ADD) *dst = __ldcg(dst) + s;
+            double* dst = ws + (int64_t)(D.out_row + rr) * r + c;
+            if (D.mode == SEG_STORE) *dst = s;
+            else if (D.mode == SEG_ADD) *dst = __ldcg(dst) + s;
             else atomicAdd(dst, s);
         }
     }
 }
 
-struct PassArgs {
-    const Segment* seg;
-    const Chunk* chunk;
-    const Piece* piece;
-    const unsigned char* arena;
-    double* ws;
-    double* u2;
-    const int32_t* perm;
-    int* err;
-    int64_t N;
-    int nseg;
-    int r;
-    int stages;
-    int stage_bytes;
-};
-
-// Producer cursor over the chunks of the segments blockIdx.x, +gridDim.x, ...
-struct Cursor {
-    int seg, ci;
-    __device__ int next(const PassArgs& a) {
-        while (seg < a.nseg) {
-            const Segment s = a.seg[seg];
-            if (ci < s.nchunks) return s.chunk0 + ci++;
-            seg += gridDim.x;
-            ci = 0;
-        }
-        return -1;
-    }
-};
-
-// One pass, segments assigned round-robin (the host sorts them longest first).
-template <int RT>
-__global__ void __launch_bounds__(kThreads, 1) k_pass(const PassArgs a) {
+// Shared-memory layout of the segment kernel (dynamic part):
+//   stages x stage_bytes             matrix chunks (bulk copies)
+//   stages x kMaxChunkCols*RT*8      the chunks' input values
+//   kConsumers * RT doubles          partial sums of the row groups
+//   stages x 2 + 1 mbarriers         full[], empty[], segment barrier
+//
+// Warp specialisation.  The producer warp (the last warp) walks this CTA's
+// chunks: it waits until the consumers released the stage, issues the bulk
+// copy of the chunk's matrices, waits (dataflow form, first chunk of a
+// segment, bounded) until the regions the segment reads are complete, copies
+// the chunk's input values into the stage, publishes a descriptor and
+// arrives on the stage's `full` barrier, which completes when the copy has
+// landed.  The 8 consumer warps wait on `full`, multiply, release the stage
+// on `empty` and, at the end of a segment, reduce and write it (and signal
+// its region), synchronising among themselves on an mbarrier.  No CTA-wide
+// barrier is taken per chunk and no wait is unbounded.
+template <int RT, bool FLOW>
+__global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
+    const int S = a.stages;
+    constexpr size_t kXin = sizeof(double) * kMaxChunkCols * RT;
     unsigned char* stage_base = smem;
-    double* red = reinterpret_cast<double*>(smem + (size_t)a.stages * a.stage_bytes);
-    unsigned char* xin = reinterpret_cast<unsigned char*>(red + kThreads * RT);
-    uint64_t* full = reinterpret_cast<uint64_t*>(xin + (size_t)kMaxChunkCols * RT * 8);
+    unsigned char* xbase = smem + (size_t)S * a.stage_bytes;
+    double* red = reinterpret_cast<double*>(xbase + (size_t)S * kXin);
+    uint64_t* full = reinterpret_cast<uint64_t*>(red + kConsumers * RT);
+    uint64_t* empty = full + S;
+    uint64_t* segbar = empty + S;
+    __shared__ StageDesc sd[kMaxStages];
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x;
-    const int r = a.r;
-    Cursor prod{(int)blockIdx.x, 0};
-    int issued = 0;   // chunks issued (thread 0)
     if (tid == 0) {
         abort_flag = 0;
-        for (int s = 0; s < a.stages; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 2);
+            mbar_init(&empty[s], kConsumers);
+        }
+        mbar_init(segbar, kConsumers);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (tid == 0) {
-        for (int s = 0; s < a.stages; ++s) {
-            const int c = prod.next(a);
-            if (c < 0) break;
-            const Chunk ch = a.chunk[c];
-            tma_load(stage_base + (size_t)s * a.stage_bytes, a.arena + ch.src, (uint32_t)ch.bytes, &full[s]);
-            ++issued;
-        }
-    }
+    volatile int* abortp = &abort_flag;
+    int issued = 0;   // producer: chunks whose copy was issued
 
-    int it = 0;   // chunks consumed
-    for (int sg = blockIdx.x; sg < a.nseg; sg += gridDim.x) {
-        const Segment S = a.seg[sg];
-        const int nrows = S.nrows;
-        const int G = kThreads / nrows;
-        const int row = tid % nrows, g = tid / nrows;
-        const bool active = g < G;
+    if (tid >= kConsumers) {
+        // ---------------- producer warp ----------------
+        const int lane = tid & 31;
+        Cursor<FLOW> cur;
+        for (int i = 0;; ++i) {
+            const int st = i % S;
+            if (i >= S) {
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait_or_abort(&empty[st], (uint32_t)((i / S) - 1) & 1u, abortp);
+                if (!__shfl_sync(~0u, ok, 0)) break;
+            }
+            int sg = -1, ci = 0;
+            if (lane == 0) cur.next(a, sg, ci);
+            sg = __shfl_sync(~0u, sg, 0);
+            ci = __shfl_sync(~0u, ci, 0);
+            if (sg < 0) {   // end marker: complete the phase without a copy
+                if (lane == 0) {
+                    sd[st].seg = -1;
+                    mbar_arrive(&full[st]);
+                    mbar_arrive(&full[st]);
+                }
+                break;
+            }
+            const FlowSeg F = a.seg[sg];
+            const Chunk C = a.chunk[F.s.chunk0 + ci];
+            if (lane == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tma_load(stage_base + (size_t)st * a.stage_bytes, a.arena + C.src, (uint32_t)C.bytes, &full[st]);
+            }
+            ++issued;
+            bool ok = true;
+            if (FLOW && ci == 0 && lane == 0) ok = deps_wait(a, sg, abortp);
+            if (!__shfl_sync(~0u, ok, 0)) {
+                if (lane == 0) {
+                    atomicExch(a.err, 1);
+                    abort_flag = 1;
+                    sd[st].seg = -1;
+                    mbar_arrive(&full[st]);
+                }
+                break;
+            }
+            stage_inputs<RT>(a, C, xbase + (size_t)st * kXin, lane);
+            __syncwarp();
+            if (lane == 0) {
+                StageDesc D;
+                D.seg = sg;
+                D.last = ci == F.s.nchunks - 1;
+                D.piece0 = C.piece0;
+                D.npieces = C.npieces;
+                D.out_row = F.s.out_row;
+                D.nrows = F.s.nrows;
+                D.mode = F.s.mode;
+                D.signal = F.signal;
+                sd[st] = D;
+                mbar_arrive(&full[st]);
+            }
+        }
+    } else {
+        // ---------------- consumer warps ----------------
+        const int r = a.r;
         double acc[RT];
 #pragma unroll
         for (int c = 0; c < RT; ++c) acc[c] = 0.0;
-
-        for (int ci = 0; ci < S.nchunks; ++ci) {
-            const int st = it % a.stages;
-            const uint32_t parity = (uint32_t)(it / a.stages) & 1u;
-            if (!mbar_wait(&full[st], parity)) abort_flag = 1;
-            const Chunk C = a.chunk[S.chunk0 + ci];
-            stage_inputs<RT>(C, a.piece, a.ws, r, xin);
-            __syncthreads();   // staged inputs visible
-            if (active)
-                consume_chunk<RT>(stage_base + (size_t)st * a.stage_bytes, C, a.piece, xin, r, nrows,
-                                  row, g, G, acc);
-            __syncthreads();   // every thread is done with stage st
-            if (abort_flag) goto bail;
-            if (tid == 0) {
-                const int c = prod.next(a);
-                if (c >= 0) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    const Chunk ch = a.chunk[c];
-                    tma_load(stage_base + (size_t)st * a.stage_bytes, a.arena + ch.src, (uint32_t)ch.bytes,
-                             &full[st]);
-                    ++issued;
-                }
+        uint32_t segphase = 0;
+        for (int i = 0;; ++i) {
+            const int st = i % S;
+            if (!mbar_wait_or_abort(&full[st], (uint32_t)(i / S) & 1u, abortp)) {
+                atomicExch(a.err, 1);
+                abort_flag = 1;
+                break;
             }
-            ++it;
-        }
-        if (active) {
+            const StageDesc D = sd[st];
+            if (D.seg < 0) break;
+            const int nrows = D.nrows;
+            const int G = kConsumers / nrows;
+            const int row = tid % nrows, g = tid / nrows;
+            if (g < G)
+                consume_chunk<RT>(stage_base + (size_t)st * a.stage_bytes, D.piece0, D.npieces, a.piece,
+                                  xbase + (size_t)st * kXin, r, nrows, row, g, G, acc);
+            mbar_arrive(&empty[st]);
+            if (D.last) {
+                if (g < G) {
 #pragma unroll
-            for (int c = 0; c < RT; ++c) red[tid * RT + c] = acc[c];
-        }
-        __syncthreads();
-        write_segment<RT>(S, S.mode, red, r, G, a.ws, a.u2, a.perm, a.N);
-        __syncthreads();
-    }
-    return;
-
-bail:
-    // a bulk copy did not complete in time: report it, let the copies still in
-    // flight land (bounded), and leave
-    if (tid == 0) {
-        atomicExch(a.err, 1);
-        for (int j = it; j < issued; ++j) {
-            const int st = j % a.stages;
-            (void)mbar_wait(&full[st], (uint32_t)(j / a.stages) & 1u);
+                    for (int c = 0; c < RT; ++c) red[tid * RT + c] = acc[c];
+                }
+#pragma unroll
+                for (int c = 0; c < RT; ++c) acc[c] = 0.0;
+                mbar_arrive(segbar);
+                if (!mbar_wait_or_abort(segbar, segphase++ & 1u, abortp)) {
+                    atomicExch(a.err, 1);
+                    abort_flag = 1;
+                    break;
+                }
+                write_segment<RT>(D, red, r, G, a.ws, a.u2, a.perm, a.N);
+                if (FLOW) __threadfence();
+                mbar_arrive(segbar);
+                if (!mbar_wait_or_abort(segbar, segphase++ & 1u, abortp)) {
+                    atomicExch(a.err, 1);
+                    abort_flag = 1;
+                    break;
+                }
+                if (FLOW && tid == 0 && D.signal >= 0) signal_region(a.cnt + D.signal);
+            }
         }
     }
     __syncthreads();
-}
-
-struct FlowArgs {
-    const FlowSeg* seg;
-    const Chunk* chunk;
-    const Piece* piece;
-    const int32_t* deps;
-    const int32_t* expect;
-    int32_t* cnt;            // region counters, then the ticket counter at [nreg]
-    const unsigned char* arena;
-    double* ws;
-    double* u2;
-    const int32_t* perm;
-    int* err;
-    int64_t N;
-    int nseg;
-    int nreg;
-    int r;
-    int stages;
-    int stage_bytes;
-};
-
-// Producer side of the flow kernel (thread 0 only): hands out chunks of the
-// segments this CTA took, taking a new ticket when a segment is exhausted.
-struct FlowCursor {
-    int seg, ci, qhead, done;
-    __device__ int next(const FlowArgs& a, int* queue) {
-        while (true) {
-            if (seg >= 0 && ci < a.seg[seg].s.nchunks) return a.seg[seg].s.chunk0 + ci++;
-            if (done) return -1;
-            const int t = atomicAdd(a.cnt + a.nreg, 1);
-            if (t >= a.nseg) {
-                queue[qhead++ % kQueue] = -1;
-                done = 1;
-                return -1;
-            }
-            queue[qhead++ % kQueue] = t;
-            seg = t;
-            ci = 0;
-        }
+    // after an abort, let the producer's copies still in flight land (bounded)
+    if (tid == kConsumers && abort_flag) {
+        for (int j = issued > S ? issued - S : 0; j < issued; ++j)
+            (void)mbar_wait(&full[j % S], (uint32_t)(j / S) & 1u);
     }
-};
-
-#ifdef H2_TRACE
-// Per-segment timeline (diagnostic builds only): ticket, SM, start, inputs
-// ready, end (globaltimer ns).
-__device__ long long g_h2_trace[1 << 22];
-__device__ __forceinline__ unsigned smid() {
-    unsigned v;
-    asm volatile("mov.u32 %0, %%smid;" : "=r"(v));
-    return v;
-}
-#endif
-
-template <int RT>
-__global__ void __launch_bounds__(kThreads, 1) k_flow(const FlowArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char* stage_base = smem;
-    double* red = reinterpret_cast<double*>(smem + (size_t)a.stages * a.stage_bytes);
-    unsigned char* xin = reinterpret_cast<unsigned char*>(red + kThreads * RT);
-    uint64_t* full = reinterpret_cast<uint64_t*>(xin + (size_t)kMaxChunkCols * RT * 8);
-    __shared__ int queue[kQueue];
-    __shared__ int abort_flag;
-
-    const int tid = threadIdx.x;
-    const int r = a.r;
-    FlowCursor prod{-1, 0, 0, 0};
-    int issued = 0;
-    if (tid == 0) {
-        abort_flag = 0;
-        for (int s = 0; s < a.stages; ++s) mbar_init(&full[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int s = 0; s < a.stages; ++s) {
-            const int c = prod.next(a, queue);
-            if (c < 0) break;
-            const Chunk ch = a.chunk[c];
-            tma_load(stage_base + (size_t)s * a.stage_bytes, a.arena + ch.src, (uint32_t)ch.bytes, &full[s]);
-            ++issued;
-        }
-        if (issued == 0) queue[0] = -1;   // no work left for this CTA
-    }
-
-    int it = 0, qtail = 0;
-    while (true) {
-        __syncthreads();   // queue entry of the next segment is visible
-        const int sg = queue[qtail++ % kQueue];
-        if (sg < 0) break;
-        const FlowSeg F = a.seg[sg];
-        const Segment S = F.s;
-#ifdef H2_TRACE
-        long long tr0 = (long long)now_ns();
-#endif
-        // wait until every region this segment reads is complete
-        if (tid == 0) {
-            for (int d = F.dep0; d < F.dep0 + F.ndep && !abort_flag; ++d) {
-                const int reg = a.deps[d];
-                const int want = a.expect[reg];
-                if (ld_acquire(a.cnt + reg) >= want) continue;
-                const unsigned long long t0 = now_ns();
-                while (ld_acquire(a.cnt + reg) < want) {
-                    if (ld_acquire(a.err) != 0 || now_ns() - t0 > kWaitNs) {
-                        abort_flag = 1;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-        }
-        __syncthreads();
-        if (abort_flag) goto bail;
-#ifdef H2_TRACE
-        long long tr1 = (long long)now_ns();
-#endif
-
-        const int nrows = S.nrows;
-        const int G = kThreads / nrows;
-        const int row = tid % nrows, g = tid / nrows;
-        const bool active = g < G;
-        double acc[RT];
-#pragma unroll
-        for (int c = 0; c < RT; ++c) acc[c] = 0.0;
-        for (int ci = 0; ci < S.nchunks; ++ci) {
-            const int st = it % a.stages;
-            const uint32_t parity = (uint32_t)(it / a.stages) & 1u;
-            if (!mbar_wait(&full[st], parity)) abort_flag = 1;
-            const Chunk C = a.chunk[S.chunk0 + ci];
-            stage_inputs<RT>(C, a.piece, a.ws, r, xin);
-            __syncthreads();   // staged inputs visible
-            if (active)
-                consume_chunk<RT>(stage_base + (size_t)st * a.stage_bytes, C, a.piece, xin, r, nrows,
-                                  row, g, G, acc);
-            __syncthreads();
-            if (abort_flag) goto bail;
-            if (tid == 0) {
-                const int c = prod.next(a, queue);
-                if (c >= 0) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    const Chunk ch = a.chunk[c];
-                    tma_load(stage_base + (size_t)st * a.stage_bytes, a.arena + ch.src, (uint32_t)ch.bytes,
-                             &full[st]);
-                    ++issued;
-                }
-            }
-            ++it;
-        }
-        if (active) {
-#pragma unroll
-            for (int c = 0; c < RT; ++c) red[tid * RT + c] = acc[c];
-        }
-        __syncthreads();
-        write_segment<RT>(S, S.mode, red, r, G, a.ws, a.u2, a.perm, a.N);
-        __threadfence();
-        __syncthreads();
-        if (tid == 0 && F.signal >= 0) atomicAdd(a.cnt + F.signal, 1);
-#ifdef H2_TRACE
-        if (tid == 0 && 5 * (sg + 1) < (1 << 22)) {
-            long long* t = g_h2_trace + 5 * sg;
-            t[0] = sg; t[1] = (long long)F.kind * 1000000 + smid() * 1000 + blockIdx.x % 1000; t[2] = tr0; t[3] = tr1;
-            t[4] = (long long)now_ns();
-        }
-#endif
-    }
-    return;
-
-bail:
-    if (tid == 0) {
-        atomicExch(a.err, 1);
-        for (int j = it; j < issued; ++j) {
-            const int st = j % a.stages;
-            (void)mbar_wait(&full[st], (uint32_t)(j / a.stages) & 1u);
-        }
-    }
-    __syncthreads();
 }
 
 // Gathers the input into tree order (workspace rows [0, N)), clears the
@@ -522,16 +489,24 @@ __global__ void k_prologue(const double* __restrict__ u1, double* __restrict__ w
     for (int64_t idx = i0; idx < nclear; idx += stride) clear[idx] = 0;
 }
 
+// Shared-memory stages of the segment kernel for r <= rt right-hand sides.
+int stages_for(int rt) { return rt >= 32 ? 2 : 3; }
+
 int rt_for(int r) {
     int rt = 1;
     while (rt < r) rt *= 2;
     return rt;
 }
 
+// Allows `smem` bytes of dynamic shared memory and asks for the largest
+// shared-memory carveout, so that as many CTAs as fit are resident per SM.
 template <class F>
 cudaError_t set_smem(F* kernel, size_t smem, size_t& configured) {
     if (configured >= smem) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess) configured = smem;
     return e;
 }
@@ -541,7 +516,7 @@ template <class F>
 int ctas_per_sm(F* kernel, size_t smem, int& cached, size_t& cached_smem) {
     if (cached > 0 && cached_smem == smem) return cached;
     int n = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kThreads, smem) != cudaSuccess || n < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kBlock, smem) != cudaSuccess || n < 1) {
         cudaGetLastError();
         n = 1;
     }
@@ -550,47 +525,44 @@ int ctas_per_sm(F* kernel, size_t smem, int& cached, size_t& cached_smem) {
     return n;
 }
 
-template <int RT>
-cudaError_t launch_pass_rt(const PassArgs& a, int grid, size_t smem, cudaStream_t s) {
+// Launches `nsm` x (resident CTAs per SM) CTAs (at most one per segment);
+// *launched receives the grid size.
+template <int RT, bool FLOW>
+cudaError_t launch_seg_rt(const KArgs& a, int nsm, size_t smem, cudaStream_t s, int* launched) {
     static size_t configured = 0, occ_smem = 0;
     static int occ = 0;
-    cudaError_t e = set_smem(k_pass<RT>, smem, configured);
+    cudaError_t e = set_smem(k_seg<RT, FLOW>, smem, configured);
     if (e != cudaSuccess) return e;
-    const int g = std::max(1, std::min(a.nseg, grid * ctas_per_sm(k_pass<RT>, smem, occ, occ_smem)));
-    k_pass<RT><<<g, kThreads, smem, s>>>(a);
+    const int g = std::max(1, std::min(a.nseg, nsm * ctas_per_sm(k_seg<RT, FLOW>, smem, occ, occ_smem)));
+    if (launched) *launched = g;
+    k_seg<RT, FLOW><<<g, kBlock, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pass(const PassArgs& a, int rt, int grid, size_t smem, cudaStream_t s) {
-    switch (rt) {
-        case 1: return launch_pass_rt<1>(a, grid, smem, s);
-        case 2: return launch_pass_rt<2>(a, grid, smem, s);
-        case 4: return launch_pass_rt<4>(a, grid, smem, s);
-        case 8: return launch_pass_rt<8>(a, grid, smem, s);
-        case 16: return launch_pass_rt<16>(a, grid, smem, s);
-        default: return launch_pass_rt<32>(a, grid, smem, s);
+template <int RT>
+int seg_occupancy(size_t smem) {
+    static size_t configured = 0;
+    if (set_smem(k_seg<RT, true>, smem, configured) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
     }
+    int n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seg<RT, true>, kBlock, smem) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n;
 }
 
-template <int RT>
-cudaError_t launch_flow_rt(const FlowArgs& a, int grid, size_t smem, cudaStream_t s) {
-    static size_t configured = 0, occ_smem = 0;
-    static int occ = 0;
-    cudaError_t e = set_smem(k_flow<RT>, smem, configured);
-    if (e != cudaSuccess) return e;
-    const int g = std::max(1, std::min(a.nseg, grid * ctas_per_sm(k_flow<RT>, smem, occ, occ_smem)));
-    k_flow<RT><<<g, kThreads, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_flow(const FlowArgs& a, int rt, int grid, size_t smem, cudaStream_t s) {
+template <bool FLOW>
+cudaError_t launch_seg(const KArgs& a, int rt, int nsm, size_t smem, cudaStream_t s, int* launched) {
     switch (rt) {
-        case 1: return launch_flow_rt<1>(a, grid, smem, s);
-        case 2: return launch_flow_rt<2>(a, grid, smem, s);
-        case 4: return launch_flow_rt<4>(a, grid, smem, s);
-        case 8: return launch_flow_rt<8>(a, grid, smem, s);
-        case 16: return launch_flow_rt<16>(a, grid, smem, s);
-        default: return launch_flow_rt<32>(a, grid, smem, s);
+        case 1: return launch_seg_rt<1, FLOW>(a, nsm, smem, s, launched);
+        case 2: return launch_seg_rt<2, FLOW>(a, nsm, smem, s, launched);
+        case 4: return launch_seg_rt<4, FLOW>(a, nsm, smem, s, launched);
+        case 8: return launch_seg_rt<8, FLOW>(a, nsm, smem, s, launched);
+        case 16: return launch_seg_rt<16, FLOW>(a, nsm, smem, s, launched);
+        default: return launch_seg_rt<32, FLOW>(a, nsm, smem, s, launched);
     }
 }
 
@@ -634,45 +606,35 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
         H2_CUDA_TRY(cudaGetLastError());
     }
     H2_CUDA_TRY(mark());
+    KArgs a{};
+    a.arena = op->d_arena;
+    a.ws = ws;
+    a.u2 = u2;
+    a.perm = op->d_perm;
+    a.err = op->d_err;
+    a.N = N;
+    a.r = r;
+    a.stages = stages_for(rt);
+    a.stage_bytes = op->stage_bytes;
     if (flow) {
-        FlowArgs a{};
         a.seg = op->d_fseg;
         a.chunk = op->d_fchunk;
         a.piece = op->d_fpiece;
         a.deps = op->d_fdeps;
         a.expect = op->d_fexpect;
         a.cnt = op->d_fcnt;
-        a.arena = op->d_arena;
-        a.ws = ws;
-        a.u2 = u2;
-        a.perm = op->d_perm;
-        a.err = op->d_err;
-        a.N = N;
         a.nseg = (int)op->fseg.size();
         a.nreg = 3 * op->nc;
-        a.r = r;
-        a.stages = op->stages;
-        a.stage_bytes = op->stage_bytes;
-        H2_CUDA_TRY(launch_flow(a, rt, op->flow_grid, smem, s));
+        H2_CUDA_TRY(launch_seg<true>(a, rt, op->nsm, smem, s, &op->flow_grid));
         H2_CUDA_TRY(mark());
         return H2_OK;
     }
-    for (const Pass& p : op->passes) {
-        PassArgs a{};
+    for (Pass& p : op->passes) {
         a.seg = p.d_seg;
         a.chunk = p.d_chunk;
         a.piece = p.d_piece;
-        a.arena = op->d_arena;
-        a.ws = ws;
-        a.u2 = u2;
-        a.perm = op->d_perm;
-        a.err = op->d_err;
-        a.N = N;
         a.nseg = (int)p.seg.size();
-        a.r = r;
-        a.stages = op->stages;
-        a.stage_bytes = op->stage_bytes;
-        H2_CUDA_TRY(launch_pass(a, rt, p.grid, smem, s));
+        H2_CUDA_TRY(launch_seg<false>(a, rt, op->nsm, smem, s, &p.grid));
         H2_CUDA_TRY(mark());
     }
     return H2_OK;
@@ -681,8 +643,36 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
 }  // namespace
 
 size_t pass_smem_bytes(const h2_handle* op, int rt) {
-    return (size_t)op->stages * op->stage_bytes + sizeof(double) * kThreads * rt +
-           sizeof(double) * kMaxChunkCols * rt + sizeof(uint64_t) * op->stages;
+    const size_t S = (size_t)stages_for(rt);
+    return S * op->stage_bytes + S * sizeof(double) * kMaxChunkCols * rt + sizeof(double) * kConsumers * rt +
+           sizeof(uint64_t) * (2 * S + 1);
+}
+
+// Resident CTAs and per-CTA rates of the dataflow kernel on the current
+// device for the operator's largest r (input of the ticket-order simulation).
+int flow_model(h2_handle* op, FlowModel& fm) {
+    int dev = 0, nsm = 0, khz = 0;
+    H2_CUDA_TRY(cudaGetDevice(&dev));
+    H2_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    H2_CUDA_TRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    const int rt = rt_for(op->params.max_rhs);
+    const size_t smem = pass_smem_bytes(op, rt);
+    int occ = 1;
+    switch (rt) {
+        case 1: occ = seg_occupancy<1>(smem); break;
+        case 2: occ = seg_occupancy<2>(smem); break;
+        case 4: occ = seg_occupancy<4>(smem); break;
+        case 8: occ = seg_occupancy<8>(smem); break;
+        case 16: occ = seg_occupancy<16>(smem); break;
+        default: occ = seg_occupancy<32>(smem); break;
+    }
+    const double ghz = khz > 0 ? khz * 1e-6 : 2.07;
+    fm.workers = nsm * occ;
+    fm.r = op->params.max_rhs;
+    fm.f64_per_ns = 2.0 * ghz / occ;
+    fm.f32_per_ns = 128.0 * ghz / occ;
+    fm.bytes_per_ns = 6800.0 / fm.workers;
+    return H2_OK;
 }
 
 int upload_plan(h2_handle* op) {
@@ -691,11 +681,14 @@ int upload_plan(h2_handle* op) {
     H2_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     int rc;
     for (Pass& p : op->passes) {
-        if ((rc = upload_vec(p.seg, &p.d_seg)) || (rc = upload_vec(p.chunk, &p.d_chunk)) ||
+        std::vector<FlowSeg> fs(p.seg.size());
+        for (size_t i = 0; i < p.seg.size(); ++i) fs[i] = FlowSeg{p.seg[i], -1, 0, 0, p.kind};
+        if ((rc = upload_vec(fs, &p.d_seg)) || (rc = upload_vec(p.chunk, &p.d_chunk)) ||
             (rc = upload_vec(p.piece, &p.d_piece)))
             return rc;
-        p.grid = nsm;
+        p.grid = 0;
     }
+    op->nsm = nsm;
     if ((rc = upload_vec(op->zero_rows, &op->d_zero_rows))) return rc;
     if (op->use_flow) {
         if ((rc = upload_vec(op->fseg, &op->d_fseg)) || (rc = upload_vec(op->fchunk, &op->d_fchunk)) ||
@@ -704,7 +697,6 @@ int upload_plan(h2_handle* op) {
             (rc = upload_vec(op->fzero_rows, &op->d_fzero_rows)))
             return rc;
         H2_CUDA_TRY(cudaMalloc((void**)&op->d_fcnt, sizeof(int32_t) * (3 * (size_t)op->nc + 1)));
-        op->flow_grid = nsm;
     }
     H2_CUDA_TRY(cudaMalloc((void**)&op->d_ws, sizeof(double) * (size_t)op->ws_rows * op->params.max_rhs));
     H2_CUDA_TRY(cudaMalloc((void**)&op->d_err, sizeof(int)));

@@ -15,6 +15,8 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <queue>
+#include <utility>
 
 #include "h2_internal.h"
 
@@ -90,6 +92,7 @@ void emit_pass(h2_handle* op, const char* name, int32_t kind, std::vector<SegSpe
                 p.piece.push_back(pc);
                 cur.npieces++;
                 cur_cols += m.ncols;
+                cur.ncols = cur_cols;
                 cur.bytes = (int32_t)(arena + mbytes - cur.src);
             } else {
                 close();
@@ -103,6 +106,7 @@ void emit_pass(h2_handle* op, const char* name, int32_t kind, std::vector<SegSpe
                     ch.bytes = (int32_t)round16((int64_t)cc * s.nrows * es);
                     ch.piece0 = (int32_t)p.piece.size();
                     ch.npieces = 1;
+                    ch.ncols = cc;
                     Piece pc{};
                     pc.smem_off = 0;
                     pc.in_row = m.in_row + c0;
@@ -199,7 +203,7 @@ void build_plan(h2_handle* op) {
         std::vector<std::vector<int32_t>> by_t(nc);
         for (size_t b = 0; b < op->far_t.size(); ++b) by_t[op->far_t[b]].push_back((int32_t)b);
         const int64_t nfar = (int64_t)op->far_t.size();
-        const int split = 8;
+        const int split = op->coupling_split;
         std::vector<SegSpec> segs;
         op->zero_rows.clear();
         for (int t = 0; t < nc; ++t) {
@@ -295,11 +299,20 @@ void build_plan(h2_handle* op) {
     }
 }
 
-// Single-launch dataflow form: every segment of every pass in one list, in
-// a topological order of the data dependencies that also puts the critical
-// path (upward chain -> coupling of the upper targets -> downward chain)
-// early and uses the near field (no dependencies) to fill the upward phase.
-void build_flow(h2_handle* op) {
+// Single-launch dataflow form: every segment of every pass in one list of
+// "tickets" that the CTAs of one persistent launch take in order.  A segment
+// may only follow the producers of the regions it reads, and a CTA that
+// takes a segment whose inputs are not complete waits for them, so the
+// order decides how much time is lost waiting.  It is chosen by simulating
+// `workers` CTAs on the host: each free CTA takes, among the segments whose
+// producers are all placed, the one with the longest remaining path to the
+// end of the product (critical path first) among those whose inputs will be
+// complete by then, else the one whose inputs complete first.  Segment cost:
+// a fixed overhead plus the larger of its FP64 multiply-adds, FP32
+// multiply-adds and matrix bytes at one CTA's share of the SM and HBM rates.
+// Returns the simulated makespan in microseconds (or -1 if the dataflow form
+// could not be built; the level-wise launches are used then).
+double build_flow(h2_handle* op, const FlowModel& fm) {
     const int nc = op->nc;
     const int kp = op->kp;
     const int64_t N = op->geom->N;
@@ -321,25 +334,29 @@ void build_flow(h2_handle* op) {
     for (int c = 0; c < nc; ++c)
         if (op->child0[c] < 0) leaf_at[op->start[c]] = c;
 
-    struct Item { FlowSeg fs; std::vector<int32_t> deps; int level; };
-    std::vector<Item> up_leaf, near, vexp_all;
-    std::vector<std::vector<Item>> up_lv, coup_lv(op->nlevels), down_lv(op->nlevels + 1),
-        vexp_lv(op->nlevels);
+    struct Item {
+        FlowSeg fs;
+        std::vector<int32_t> deps;
+        double cost = 0.0, blevel = 0.0;
+    };
+    std::vector<Item> items;
     std::vector<char> zero(nc, 0);
-
+    const double r = std::max(1, fm.r);
     for (const Pass& p : op->passes) {
-        std::vector<Item> items;
         for (const Segment& sg0 : p.seg) {
             Item it{};
             it.fs.s = sg0;
             it.fs.kind = p.kind;
             it.fs.s.chunk0 = (int32_t)op->fchunk.size();
+            double mac64 = 0.0, mac32 = 0.0, bytes = 0.0;
             for (int q = 0; q < sg0.nchunks; ++q) {
                 Chunk ch = p.chunk[(size_t)sg0.chunk0 + q];
                 const int32_t pbase = (int32_t)op->fpiece.size();
+                bytes += ch.bytes;
                 for (int u = 0; u < ch.npieces; ++u) {
                     const Piece pc = p.piece[(size_t)ch.piece0 + u];
                     op->fpiece.push_back(pc);
+                    (pc.type == PIECE_F64 ? mac64 : mac32) += (double)sg0.nrows * pc.ncols * r;
                     int rb;
                     const int c = cluster_of_row(pc.in_row, rb);
                     if (c >= 0) {
@@ -351,10 +368,10 @@ void build_flow(h2_handle* op) {
                 ch.piece0 = pbase;
                 op->fchunk.push_back(ch);
             }
-            // output region and level
-            int c = -1;
+            it.cost = fm.seg_ns + fm.chunk_ns * sg0.nchunks +
+                      std::max({mac64 / fm.f64_per_ns, mac32 / fm.f32_per_ns, bytes / fm.bytes_per_ns});
             if (sg0.mode == SEG_FINAL || sg0.mode == SEG_FINAL_ADD) {
-                c = leaf_at[sg0.out_row];
+                const int c = leaf_at[sg0.out_row];
                 if (sg0.mode == SEG_FINAL) it.fs.signal = 2 * nc + c;
                 else {
                     it.fs.signal = -1;
@@ -362,61 +379,94 @@ void build_flow(h2_handle* op) {
                 }
             } else {
                 int rb;
-                c = cluster_of_row(sg0.out_row, rb);
+                const int c = cluster_of_row(sg0.out_row, rb);
                 it.fs.signal = rb + c;
                 if (rb == nc) {   // y-hat: every producer accumulates atomically
                     it.fs.s.mode = SEG_ATOMIC;
                     zero[c] = 1;
                 }
             }
-            it.level = op->level[c];
             if (it.fs.signal >= 0) op->fexpect[it.fs.signal]++;
             items.push_back(std::move(it));
         }
-        switch (p.kind) {
-            case PASS_UP_LEAF: for (auto& i : items) up_leaf.push_back(std::move(i)); break;
-            case PASS_UP_TRANSFER: up_lv.push_back(std::move(items)); break;
-            case PASS_COUPLING: for (auto& i : items) coup_lv[i.level].push_back(std::move(i)); break;
-            case PASS_DOWN_TRANSFER: for (auto& i : items) down_lv[i.level].push_back(std::move(i)); break;
-            case PASS_LEAF_NEAR: for (auto& i : items) near.push_back(std::move(i)); break;
-            case PASS_LEAF_EXPAND: for (auto& i : items) vexp_lv[i.level].push_back(std::move(i)); break;
-            default: return;
+    }
+    const int nreg = 3 * nc;
+    const int n = (int)items.size();
+    // consumers of every region
+    std::vector<std::vector<int32_t>> consumers(nreg);
+    for (int i = 0; i < n; ++i)
+        for (int32_t d : items[i].deps) consumers[d].push_back(i);
+    // longest path to the end: the passes are listed in a topological order,
+    // so one sweep in reverse settles every consumer before its producers
+    std::vector<double> reg_blevel(nreg, 0.0);
+    for (int i = n - 1; i >= 0; --i) {
+        Item& it = items[i];
+        it.blevel = it.cost + (it.fs.signal >= 0 ? reg_blevel[it.fs.signal] : 0.0);
+        for (int32_t d : it.deps) reg_blevel[d] = std::max(reg_blevel[d], it.blevel);
+    }
+    // list scheduling on `workers` simulated CTAs
+    std::vector<int32_t> reg_left(op->fexpect.begin(), op->fexpect.end());
+    std::vector<double> reg_done(nreg, 0.0);
+    std::vector<int32_t> deps_left(n);
+    std::vector<double> ready_at(n, 0.0);
+    using Cand = std::pair<double, int32_t>;
+    std::priority_queue<Cand> ready;                                            // by b-level
+    std::priority_queue<Cand, std::vector<Cand>, std::greater<Cand>> pending;   // by ready time
+    for (int i = 0; i < n; ++i) {
+        deps_left[i] = (int32_t)items[i].deps.size();
+        for (int32_t d : items[i].deps)
+            if (reg_left[d] == 0) deps_left[i]--;   // region without producers: nothing to wait for
+        if (deps_left[i] == 0) pending.push({0.0, i});
+    }
+    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+    for (int w = 0; w < std::max(1, fm.workers); ++w) free_at.push(0.0);
+    std::vector<int32_t> order;
+    order.reserve(n);
+    double makespan = 0.0;
+    while ((int)order.size() < n) {
+        const double t = free_at.top();
+        free_at.pop();
+        while (!pending.empty() && pending.top().first <= t) {
+            ready.push({items[pending.top().second].blevel, pending.top().second});
+            pending.pop();
+        }
+        int32_t pick;
+        if (!ready.empty()) {
+            pick = ready.top().second;
+            ready.pop();
+        } else if (!pending.empty()) {
+            pick = pending.top().second;
+            pending.pop();
+        } else {
+            return -1.0;   // a region that never completes: keep the level-wise launches
+        }
+        const double start = std::max(t, ready_at[pick]);
+        const double fin = start + items[pick].cost;
+        makespan = std::max(makespan, fin);
+        free_at.push(fin);
+        order.push_back(pick);
+        const int32_t sig = items[pick].fs.signal;
+        if (sig >= 0) {
+            reg_done[sig] = std::max(reg_done[sig], fin);
+            if (--reg_left[sig] == 0) {
+                for (int32_t c : consumers[sig]) {
+                    ready_at[c] = std::max(ready_at[c], reg_done[sig]);
+                    if (--deps_left[c] == 0) pending.push({ready_at[c], c});
+                }
+            }
         }
     }
-    // ticket order
-    std::vector<Item*> order;
-    for (auto& i : up_leaf) order.push_back(&i);
-    const size_t nslices = std::max<size_t>(1, up_lv.size());
-    size_t nq = 0;
-    for (size_t l = 0; l < nslices; ++l) {
-        if (l < up_lv.size())
-            for (auto& i : up_lv[l]) order.push_back(&i);
-        const size_t end = near.size() * (l + 1) / nslices;
-        for (; nq < end; ++nq) order.push_back(&near[nq]);
-    }
-    for (; nq < near.size(); ++nq) order.push_back(&near[nq]);
-    for (int l = 0; l < op->nlevels; ++l) {
-        for (auto& i : coup_lv[l]) order.push_back(&i);
-        if (l + 1 <= op->nlevels)
-            for (auto& i : down_lv[l + 1]) order.push_back(&i);
-        for (auto& i : vexp_lv[l]) order.push_back(&i);
-    }
-    // every dependency must be produced by earlier tickets only
-    std::vector<int32_t> last_producer((size_t)3 * nc, -1);
-    for (size_t t = 0; t < order.size(); ++t)
-        if (order[t]->fs.signal >= 0) last_producer[order[t]->fs.signal] = (int32_t)t;
-    for (size_t t = 0; t < order.size(); ++t)
-        for (int32_t d : order[t]->deps)
-            if (last_producer[d] < 0 || last_producer[d] >= (int32_t)t) return;   // keep level-wise launches
-    for (Item* it : order) {
-        it->fs.dep0 = (int32_t)op->fdeps.size();
-        it->fs.ndep = (int32_t)it->deps.size();
-        for (int32_t d : it->deps) op->fdeps.push_back(d);
-        op->fseg.push_back(it->fs);
+    for (int32_t i : order) {
+        Item& it = items[i];
+        it.fs.dep0 = (int32_t)op->fdeps.size();
+        it.fs.ndep = (int32_t)it.deps.size();
+        for (int32_t d : it.deps) op->fdeps.push_back(d);
+        op->fseg.push_back(it.fs);
     }
     for (int c = 0; c < nc; ++c)
         if (zero[c]) op->fzero_rows.push_back((int32_t)(op->row_yhat + (int64_t)c * kp));
     op->use_flow = 1;
+    return makespan * 1e-3;
 }
 
 }  // namespace h2
