@@ -25,7 +25,8 @@ void free_device(h2_handle* h) {
         h2::release_graph(h);
         h2::release_profile(h);
         for (h2::Pass& p : h->passes) { f(p.d_seg); f(p.d_chunk); f(p.d_piece); }
-        f(h->d_arena); f(h->d_perm); f(h->d_box); f(h->d_ws); f(h->d_zero_rows); f(h->d_io); f(h->d_err);
+        f(h->d_arena); f(h->d_perm); f(h->d_box); f(h->d_ws); f(h->d_ws32); f(h->d_gather_src);
+        f(h->d_zero_rows); f(h->d_io); f(h->d_err);
         f(h->d_fseg); f(h->d_fchunk); f(h->d_fpiece); f(h->d_fdeps); f(h->d_fexpect); f(h->d_fzero_rows);
         f(h->d_fcnt);
     }
@@ -135,7 +136,7 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
     op->params = p;
     op->m = p.m;
     op->k = p.m * p.m * p.m;
-    op->kp = (op->k + 1) / 2 * 2;
+    op->kp = (op->k + 3) / 4 * 4;
     op->device = geom->device;
     h2::build_cluster_tree(op);
     h2::build_block_partition(op);

@@ -25,6 +25,7 @@
 #define H2_MAX_LEAF 128
 #define H2_MAX_RHS 32
 #define H2_MAX_CHUNK_COLS 128   // input columns of one chunk (shared-memory staging)
+#define H2_MAX_CHUNK_PIECES 32  // matrices of one chunk (one producer lane each)
 
 namespace h2 {
 
@@ -47,10 +48,15 @@ struct Chunk {
     int32_t piece0;      // first piece (index into the pass's piece array)
     int32_t npieces;
     int32_t ncols;       // input columns of all its pieces (<= H2_MAX_CHUNK_COLS)
+    int32_t in_row0;     // input row and type of the first piece (a one-piece chunk
+    int32_t type0;       // needs no piece-table read)
 };
 
 // One column-major matrix (nrows x ncols, nrows = the segment's) inside a
-// stage, multiplied with workspace rows [in_row, in_row + ncols).
+// stage, multiplied with workspace rows [in_row, in_row + ncols) of the FP64
+// workspace (PIECE_F64) or of the FP32 workspace (PIECE_F32).  in_row is a
+// multiple of 4, so that the input of a piece (ncols * r values) starts on a
+// 16-byte boundary in either workspace.
 struct Piece {
     int32_t smem_off;    // byte offset inside the stage (16-byte aligned)
     int32_t in_row;
@@ -59,12 +65,12 @@ struct Piece {
 };
 
 struct Segment {
-    int32_t out_row;     // workspace row (or tree position for SEG_FINAL)
+    int32_t out_row;     // workspace row (or tree position for SEG_FINAL, SEG_FINAL_ADD)
     int32_t nrows;       // <= 128
     int32_t mode;        // SegMode
     int32_t chunk0;      // first chunk
-    int32_t nchunks;
-    int32_t pad;
+    int32_t nchunks;     // >= 1
+    int32_t out_f32;     // 1: the output rows are in the FP32 workspace
 };
 
 // Host plan of one pass plus its device copies.
@@ -145,9 +151,18 @@ struct h2_handle {
     unsigned char* d_arena = nullptr;
     int32_t* d_perm = nullptr;
     double* d_box = nullptr;
-    // workspace rows: [0, N) permuted input, then x-hat and y-hat (kp rows per cluster)
+    // Workspace rows (r values per row; the same numbering in the FP64 and the
+    // FP32 workspace): the input in tree order, leaf by leaf, each leaf padded to
+    // a multiple of 4 rows (rows [0, row_xhat)); then x-hat and y-hat, kp rows
+    // per cluster; then 4 rows of tail padding.  The FP32 workspace exists for
+    // FP32 operators, whose far-field vectors (x-hat, y-hat and the copy of the
+    // input read by the leaf projections) are FP32.
     int64_t row_xhat = 0, row_yhat = 0, ws_rows = 0;
+    std::vector<int32_t> leaf_row;    // first workspace row of each cluster's input (leaves)
+    std::vector<int32_t> gather_src;  // per input row: mesh node, or -1 for padding
+    int32_t* d_gather_src = nullptr;
     double* d_ws = nullptr;
+    float* d_ws32 = nullptr;
     std::vector<int32_t> zero_rows;   // y-hat regions cleared before the coupling pass
     int32_t* d_zero_rows = nullptr;
     double* d_io = nullptr;           // device staging for host-pointer calls

@@ -96,8 +96,18 @@ __device__ __forceinline__ int ld_acquire(const int32_t* p) {
 struct StageDesc {
     int32_t seg;       // segment index (-1: this CTA has no more work)
     int32_t last;      // 1 if the chunk is the last of its segment
-    int32_t piece0, npieces;
+    int32_t npieces;
+    int32_t f32;       // 1 if the chunk's matrices and inputs are FP32
     int32_t out_row, nrows, mode, signal;
+    int32_t out_f32;   // 1 if the segment's output rows are FP32
+};
+
+// One matrix of a staged chunk, as the consumers read it.
+struct SPiece {
+    int32_t smem_off;   // byte offset of the matrix inside the stage
+    int32_t in_row;     // first workspace row of its input
+    int32_t ncols;
+    int32_t xoff;       // byte offset of its input inside the stage's input buffer
 };
 
 struct KArgs {
@@ -108,7 +118,8 @@ struct KArgs {
     const int32_t* expect;     // dataflow form only
     int32_t* cnt;              // dataflow form: region counters, ticket counter at [nreg]
     const unsigned char* arena;
-    double* ws;
+    double* ws;                // FP64 workspace
+    float* ws32;               // FP32 workspace (FP32 operators)
     double* u2;
     const int32_t* perm;
     int* err;
@@ -138,39 +149,18 @@ __device__ __forceinline__ void signal_region(int32_t* p) {
     asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(p) : "memory");
 }
 
-// The producer warp's cursor over the chunks of its CTA (lane 0).
-// FLOW: segments come from the global ticket counter (topological order);
-// otherwise segments blockIdx.x, blockIdx.x + gridDim.x, ... of one pass.
+// The producer warp's source of segments (lane 0).  FLOW: the global ticket
+// counter (topological order); otherwise segments blockIdx.x,
+// blockIdx.x + gridDim.x, ... of one pass.  Returns -1 when none is left.
 template <bool FLOW>
-struct Cursor {
-    int seg = -1, ci = 0, nchunks = 0, k = 0, done = 0;
-    __device__ void next(const KArgs& a, int& out_seg, int& out_ci) {
-        out_seg = -1;
-        out_ci = 0;
-        while (!done) {
-            if (seg >= 0 && ci < nchunks) {
-                out_seg = seg;
-                out_ci = ci++;
-                return;
-            }
-            int t;
-            if (FLOW) t = atomicAdd(a.cnt + a.nreg, 1);
-            else t = (int)blockIdx.x + (k++) * (int)gridDim.x;
-            if (t >= a.nseg) {
-                done = 1;
-                return;
-            }
-            seg = t;
-            ci = 0;
-            nchunks = a.seg[t].s.nchunks;
-        }
-    }
-};
+__device__ __forceinline__ int take_segment(const KArgs& a, int& k) {
+    const int t = FLOW ? atomicAdd(a.cnt + a.nreg, 1) : (int)blockIdx.x + (k++) * (int)gridDim.x;
+    return t < a.nseg ? t : -1;
+}
 
 // Bounded wait (lane 0 of the producer) until every region segment `sg`
 // reads has all its producers done.  False on timeout or abort.
-__device__ bool deps_wait(const KArgs& a, int sg, volatile int* abort_flag) {
-    const FlowSeg& F = a.seg[sg];
+__device__ bool deps_wait(const KArgs& a, const FlowSeg& F, volatile int* abort_flag) {
     for (int d = F.dep0; d < F.dep0 + F.ndep; ++d) {
         const int reg = a.deps[d];
         const int want = a.expect[reg];
@@ -184,57 +174,45 @@ __device__ bool deps_wait(const KArgs& a, int sg, volatile int* abort_flag) {
     return true;
 }
 
-// The producer warp copies the input values of chunk C (the workspace rows of
-// its pieces, concatenated, r values per row) into a stage's input buffer
-// laid out [column of the chunk][RT], FP64 or (FP32 chunks) FP32.  Inputs are
-// read through L2 (ld.global.cg): in the dataflow form other CTAs of the same
-// launch wrote them.
-template <int RT>
-__device__ __forceinline__ void stage_inputs(const KArgs& a, const Chunk& C, unsigned char* xin, int lane) {
-    constexpr int B = 8;   // loads in flight per lane
-    const int r = a.r;
-    const int total = C.ncols * r;
-    const bool f32 = a.piece[C.piece0].type == PIECE_F32;
-    int p = C.piece0, col0 = 0;
-    Piece P = a.piece[p];
-    for (int base = 0; base < total; base += 32 * B) {
-        double v[B];
-        int dst[B];
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-            const int idx = base + lane + 32 * j;
-            dst[j] = -1;
-            if (idx < total) {
-                const int col = idx / r, cc = idx - col * r;
-                while (col >= col0 + P.ncols) {
-                    col0 += P.ncols;
-                    P = a.piece[++p];
-                }
-                v[j] = __ldcg(a.ws + (int64_t)(P.in_row + col - col0) * r + cc);
-                dst[j] = col * RT + cc;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-            if (dst[j] < 0) continue;
-            if (f32) reinterpret_cast<float*>(xin)[dst[j]] = (float)v[j];
-            else reinterpret_cast<double*>(xin)[dst[j]] = v[j];
-        }
+// Bytes of the staged input of one piece: ncols rows of r values, rounded up
+// to 16 (the bulk copy may read up to 3 values past the piece's rows; every
+// workspace region is followed by padding or another region).
+__device__ __forceinline__ int input_bytes(int ncols, int r, bool f32) {
+    return ((ncols * r * (f32 ? 4 : 8)) + 15) & ~15;
+}
+
+// Issues the bulk copies of a chunk's inputs (lane p copies piece p's
+// workspace rows, which are contiguous) into the stage's input buffer; they
+// complete on the stage's `full` barrier.  Workspace values written by other
+// CTAs of the launch were published with release/acquire on the region
+// counters; the proxy fence orders them before these async-proxy reads.
+__device__ __forceinline__ void issue_inputs(const KArgs& a, const SPiece* pc, int npieces, bool f32,
+                                             unsigned char* xin, uint64_t* bar, int lane) {
+    if (lane < npieces) {
+        const SPiece P = pc[lane];
+        const int bytes = input_bytes(P.ncols, a.r, f32);
+        const unsigned char* src = f32 ? reinterpret_cast<const unsigned char*>(a.ws32 + (int64_t)P.in_row * a.r)
+                                       : reinterpret_cast<const unsigned char*>(a.ws + (int64_t)P.in_row * a.r);
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_addr(xin + P.xoff)),
+            "l"(src), "r"(bytes), "r"(smem_addr(bar))
+            : "memory");
     }
 }
 
 // Multiplies the pieces of one staged chunk into the thread's accumulators.
 template <int RT>
-__device__ __forceinline__ void consume_chunk(const unsigned char* stage, int piece0, int npieces,
-                                              const Piece* __restrict__ pieces, const unsigned char* xin,
-                                              int r, int nrows, int row, int g, int G, double (&acc)[RT]) {
-    int xcol = 0;
-    for (int p = piece0; p < piece0 + npieces; ++p) {
-        const Piece P = pieces[p];
+__device__ __forceinline__ void consume_chunk(const unsigned char* stage, const SPiece* pieces, int npieces,
+                                              bool f32, const unsigned char* xin, int r, int nrows, int row,
+                                              int g, int G, double (&acc)[RT]) {
+    for (int p = 0; p < npieces; ++p) {
+        const SPiece P = pieces[p];
         const int nc = P.ncols;
-        if (P.type == PIECE_F64) {
+        if (!f32) {
             const double* A = reinterpret_cast<const double*>(stage + P.smem_off) + row;
-            const double* x = reinterpret_cast<const double*>(xin) + xcol * RT;
+            const double* x = reinterpret_cast<const double*>(xin + P.xoff);
             if (RT == 1) {
                 double a0 = 0.0, a1 = 0.0;
                 int col = g;
@@ -251,12 +229,12 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, int pi
                     const double v = A[col * nrows];
 #pragma unroll
                     for (int c = 0; c < RT; ++c)
-                        if (c < r) acc[c] = fma(v, x[col * RT + c], acc[c]);
+                        if (c < r) acc[c] = fma(v, x[col * r + c], acc[c]);
                 }
             }
         } else {
             const float* A = reinterpret_cast<const float*>(stage + P.smem_off) + row;
-            const float* x = reinterpret_cast<const float*>(xin) + xcol * RT;
+            const float* x = reinterpret_cast<const float*>(xin + P.xoff);
             if (RT == 1) {
                 float a0 = 0.0f, a1 = 0.0f;
                 int col = g;
@@ -276,32 +254,43 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, int pi
                     const float v = A[col * nrows];
 #pragma unroll
                     for (int c = 0; c < RT; ++c)
-                        if (c < r) acc32[c] = fmaf(v, x[col * RT + c], acc32[c]);
+                        if (c < r) acc32[c] = fmaf(v, x[col * r + c], acc32[c]);
                 }
 #pragma unroll
                 for (int c = 0; c < RT; ++c) acc[c] += (double)acc32[c];
             }
         }
-        xcol += nc;
     }
 }
 
-// Adds the G partial sums of every row and writes the segment (consumer threads).
+// Writer warps of a segment: warp w < writer_warps(nrows) adds the G partial
+// sums of rows 32w .. 32w+31 (one row per lane, all r right-hand sides) and
+// writes them; the other consumer warps go on with the next chunk.
+__host__ __device__ constexpr int writer_warps(int nrows) { return (nrows + 31) / 32; }
+
 template <int RT>
 __device__ __forceinline__ void write_segment(const StageDesc& D, const double* red, int r, int G,
-                                              double* ws, double* u2, const int32_t* __restrict__ perm,
-                                              int64_t N) {
+                                              double* ws, float* ws32, double* u2,
+                                              const int32_t* __restrict__ perm, int64_t N) {
     const int nrows = D.nrows;
-    for (int idx = threadIdx.x; idx < nrows * r; idx += kConsumers) {
-        const int rr = idx / r, c = idx - rr * r;
+    const int rr = threadIdx.x;   // writer warps only: threadIdx.x < 32 * writer_warps(nrows)
+    if (rr >= nrows) return;
+    const bool fin = D.mode == SEG_FINAL || D.mode == SEG_FINAL_ADD;
+    const int64_t orow = fin ? (int64_t)perm[D.out_row + rr] : (int64_t)(D.out_row + rr) * r;
+    for (int c = 0; c < r; ++c) {
         double s = 0.0;
         for (int g2 = 0; g2 < G; ++g2) s += red[(g2 * nrows + rr) * RT + c];
-        if (D.mode == SEG_FINAL || D.mode == SEG_FINAL_ADD) {
-            double* dst = u2 + (int64_t)c * N + perm[D.out_row + rr];
+        if (fin) {
+            double* dst = u2 + (int64_t)c * N + orow;
             if (D.mode == SEG_FINAL) *dst = s;
             else *dst = __ldcg(dst) + s;
+        } else if (D.out_f32) {
+            float* dst = ws32 + orow + c;
+            if (D.mode == SEG_STORE) *dst = (float)s;
+            else if (D.mode == SEG_ADD) *dst = __ldcg(dst) + (float)s;
+            else atomicAdd(dst, (float)s);
         } else {
-            double* dst = ws + (int64_t)(D.out_row + rr) * r + c;
+            double* dst = ws + orow + c;
             if (D.mode == SEG_STORE) *dst = s;
             else if (D.mode == SEG_ADD) *dst = __ldcg(dst) + s;
             else atomicAdd(dst, s);
@@ -309,34 +298,49 @@ __device__ __forceinline__ void write_segment(const StageDesc& D, const double* 
     }
 }
 
+// Input buffer of one stage: at most kMaxChunkCols FP64 rows of RT values
+// plus the 16-byte rounding of every piece.
+__host__ __device__ constexpr size_t xin_bytes(int rt) {
+    return sizeof(double) * kMaxChunkCols * rt + 16 * H2_MAX_CHUNK_PIECES;
+}
+
+// Partial-sum buffers of the segment kernel: two (alternating between
+// segments, so one barrier per segment suffices) while they are small.
+__host__ __device__ constexpr int red_buffers(int rt) { return rt <= 8 ? 2 : 1; }
+
 // Shared-memory layout of the segment kernel (dynamic part):
 //   stages x stage_bytes             matrix chunks (bulk copies)
 //   stages x kMaxChunkCols*RT*8      the chunks' input values
-//   kConsumers * RT doubles          partial sums of the row groups
+//   red_buffers x kConsumers*RT*8    partial sums of the row groups
 //   stages x 2 + 1 mbarriers         full[], empty[], segment barrier
 //
 // Warp specialisation.  The producer warp (the last warp) walks this CTA's
 // chunks: it waits until the consumers released the stage, issues the bulk
-// copy of the chunk's matrices, waits (dataflow form, first chunk of a
+// copy of the chunk's matrices, copies the chunk's piece table into shared
+// memory (one piece per lane), waits (dataflow form, first chunk of a
 // segment, bounded) until the regions the segment reads are complete, copies
-// the chunk's input values into the stage, publishes a descriptor and
-// arrives on the stage's `full` barrier, which completes when the copy has
+// the chunk's input values into the stage, publishes a descriptor and arrives
+// on the stage's `full` barrier, which completes when the bulk copy has
 // landed.  The 8 consumer warps wait on `full`, multiply, release the stage
-// on `empty` and, at the end of a segment, reduce and write it (and signal
-// its region), synchronising among themselves on an mbarrier.  No CTA-wide
-// barrier is taken per chunk and no wait is unbounded.
+// on `empty` and, at the end of a segment, add the row groups' partial sums
+// (one mbarrier-based barrier among the consumers); the writer warps write
+// the segment and, in the dataflow form, each signals the segment's region
+// with a release add.  No CTA-wide barrier is taken per chunk and no
+// wait is unbounded.
 template <int RT, bool FLOW>
 __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int S = a.stages;
-    constexpr size_t kXin = sizeof(double) * kMaxChunkCols * RT;
+    constexpr size_t kXin = xin_bytes(RT);
+    constexpr int NRED = red_buffers(RT);
     unsigned char* stage_base = smem;
     unsigned char* xbase = smem + (size_t)S * a.stage_bytes;
     double* red = reinterpret_cast<double*>(xbase + (size_t)S * kXin);
-    uint64_t* full = reinterpret_cast<uint64_t*>(red + kConsumers * RT);
+    uint64_t* full = reinterpret_cast<uint64_t*>(red + NRED * kConsumers * RT);
     uint64_t* empty = full + S;
     uint64_t* segbar = empty + S;
     __shared__ StageDesc sd[kMaxStages];
+    __shared__ SPiece spc[kMaxStages][H2_MAX_CHUNK_PIECES];
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x;
@@ -355,8 +359,23 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
 
     if (tid >= kConsumers) {
         // ---------------- producer warp ----------------
+        // The next segment (its descriptor and first 32 chunk descriptors,
+        // one per lane) is fetched while the last chunk of the current one is
+        // staged, so that the latencies overlap.
         const int lane = tid & 31;
-        Cursor<FLOW> cur;
+        int k = 0;
+        int nsg = -1;
+        if (lane == 0) nsg = take_segment<FLOW>(a, k);
+        nsg = __shfl_sync(~0u, nsg, 0);
+        FlowSeg nF{};
+        Chunk nmyc{};
+        if (nsg >= 0) {
+            nF = a.seg[nsg];
+            if (lane < nF.s.nchunks) nmyc = a.chunk[nF.s.chunk0 + lane];
+        }
+        int sg = -1, ci = 0, base = 0;
+        FlowSeg F{};
+        Chunk myc{};     // chunk `base + lane` of the current segment
         for (int i = 0;; ++i) {
             const int st = i % S;
             if (i >= S) {
@@ -364,10 +383,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                 if (lane == 0) ok = mbar_wait_or_abort(&empty[st], (uint32_t)((i / S) - 1) & 1u, abortp);
                 if (!__shfl_sync(~0u, ok, 0)) break;
             }
-            int sg = -1, ci = 0;
-            if (lane == 0) cur.next(a, sg, ci);
-            sg = __shfl_sync(~0u, sg, 0);
-            ci = __shfl_sync(~0u, ci, 0);
+            if (sg < 0 || ci >= F.s.nchunks) {   // move to the prefetched segment
+                sg = nsg;
+                F = nF;
+                myc = nmyc;
+                ci = 0;
+                base = 0;
+            }
             if (sg < 0) {   // end marker: complete the phase without a copy
                 if (lane == 0) {
                     sd[st].seg = -1;
@@ -376,15 +398,54 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                 }
                 break;
             }
-            const FlowSeg F = a.seg[sg];
-            const Chunk C = a.chunk[F.s.chunk0 + ci];
+            if (ci >= base + 32) {
+                base += 32;
+                if (base + lane < F.s.nchunks) myc = a.chunk[F.s.chunk0 + base + lane];
+            }
+            const int src_lane = ci - base;
+            const long long csrc = __shfl_sync(~0u, (long long)myc.src, src_lane);
+            const int cbytes = __shfl_sync(~0u, myc.bytes, src_lane);
+            const int cpiece0 = __shfl_sync(~0u, myc.piece0, src_lane);
+            const int cnp = __shfl_sync(~0u, myc.npieces, src_lane);
+            const int cncols = __shfl_sync(~0u, myc.ncols, src_lane);
+            const int cin0 = __shfl_sync(~0u, myc.in_row0, src_lane);
+            const bool f32 = __shfl_sync(~0u, myc.type0, src_lane) == PIECE_F32;
             if (lane == 0) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                tma_load(stage_base + (size_t)st * a.stage_bytes, a.arena + C.src, (uint32_t)C.bytes, &full[st]);
+                tma_load(stage_base + (size_t)st * a.stage_bytes, a.arena + csrc, (uint32_t)cbytes, &full[st]);
             }
             ++issued;
+            const bool last = ci == F.s.nchunks - 1;
+            if (last) {   // prefetch the next segment
+                if (lane == 0) nsg = take_segment<FLOW>(a, k);
+                nsg = __shfl_sync(~0u, nsg, 0);
+                if (nsg >= 0) {
+                    nF = a.seg[nsg];
+                    if (lane < nF.s.nchunks) nmyc = a.chunk[nF.s.chunk0 + lane];
+                }
+            }
+            // piece table of the chunk (one piece per lane), with the byte
+            // offsets of the pieces' inputs in the stage's input buffer
+            int in_total;
+            if (cnp == 1) {
+                in_total = input_bytes(cncols, a.r, f32);
+                if (lane == 0) spc[st][0] = SPiece{0, cin0, cncols, 0};
+            } else {
+                Piece pc{};
+                if (lane < cnp) pc = a.piece[cpiece0 + lane];
+                const int mine = lane < cnp ? input_bytes(pc.ncols, a.r, f32) : 0;
+                int xoff = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(~0u, xoff, o);
+                    if (lane >= o) xoff += v;
+                }
+                in_total = __shfl_sync(~0u, xoff, 31);
+                xoff -= mine;   // exclusive prefix
+                if (lane < cnp) spc[st][lane] = SPiece{pc.smem_off, pc.in_row, pc.ncols, xoff};
+            }
             bool ok = true;
-            if (FLOW && ci == 0 && lane == 0) ok = deps_wait(a, sg, abortp);
+            if (FLOW && ci == 0 && lane == 0) ok = deps_wait(a, F, abortp);
             if (!__shfl_sync(~0u, ok, 0)) {
                 if (lane == 0) {
                     atomicExch(a.err, 1);
@@ -394,21 +455,27 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                 }
                 break;
             }
-            stage_inputs<RT>(a, C, xbase + (size_t)st * kXin, lane);
+            if (lane == 0)
+                asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&full[st])),
+                             "r"(in_total)
+                             : "memory");
             __syncwarp();
+            issue_inputs(a, spc[st], cnp, f32, xbase + (size_t)st * kXin, &full[st], lane);
             if (lane == 0) {
                 StageDesc D;
                 D.seg = sg;
-                D.last = ci == F.s.nchunks - 1;
-                D.piece0 = C.piece0;
-                D.npieces = C.npieces;
+                D.last = last;
+                D.npieces = cnp;
+                D.f32 = f32;
                 D.out_row = F.s.out_row;
                 D.nrows = F.s.nrows;
                 D.mode = F.s.mode;
+                D.out_f32 = F.s.out_f32;
                 D.signal = F.signal;
                 sd[st] = D;
                 mbar_arrive(&full[st]);
             }
+            ++ci;
         }
     } else {
         // ---------------- consumer warps ----------------
@@ -430,13 +497,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
             const int G = kConsumers / nrows;
             const int row = tid % nrows, g = tid / nrows;
             if (g < G)
-                consume_chunk<RT>(stage_base + (size_t)st * a.stage_bytes, D.piece0, D.npieces, a.piece,
+                consume_chunk<RT>(stage_base + (size_t)st * a.stage_bytes, spc[st], D.npieces, D.f32 != 0,
                                   xbase + (size_t)st * kXin, r, nrows, row, g, G, acc);
             mbar_arrive(&empty[st]);
             if (D.last) {
+                double* rb = red + (size_t)(segphase % NRED) * kConsumers * RT;
                 if (g < G) {
 #pragma unroll
-                    for (int c = 0; c < RT; ++c) red[tid * RT + c] = acc[c];
+                    for (int c = 0; c < RT; ++c) rb[tid * RT + c] = acc[c];
                 }
 #pragma unroll
                 for (int c = 0; c < RT; ++c) acc[c] = 0.0;
@@ -446,15 +514,20 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                     abort_flag = 1;
                     break;
                 }
-                write_segment<RT>(D, red, r, G, a.ws, a.u2, a.perm, a.N);
-                if (FLOW) __threadfence();
-                mbar_arrive(segbar);
-                if (!mbar_wait_or_abort(segbar, segphase++ & 1u, abortp)) {
-                    atomicExch(a.err, 1);
-                    abort_flag = 1;
-                    break;
+                const bool writer = (tid >> 5) < writer_warps(nrows);
+                if (writer) write_segment<RT>(D, rb, r, G, a.ws, a.ws32, a.u2, a.perm, a.N);
+                if (NRED == 1) {   // the single buffer is rewritten by the next segment
+                    mbar_arrive(segbar);
+                    if (!mbar_wait_or_abort(segbar, segphase++ & 1u, abortp)) {
+                        atomicExch(a.err, 1);
+                        abort_flag = 1;
+                        break;
+                    }
                 }
-                if (FLOW && tid == 0 && D.signal >= 0) signal_region(a.cnt + D.signal);
+                if (FLOW && writer && D.signal >= 0) {
+                    __syncwarp();
+                    if ((tid & 31) == 0) signal_region(a.cnt + D.signal);
+                }
             }
         }
     }
@@ -466,31 +539,38 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
     }
 }
 
-// Gathers the input into tree order (workspace rows [0, N)), clears the
-// y-hat rows that are accumulated atomically, and clears `nclear` ints (the
-// flow kernel's region and ticket counters).
-__global__ void k_prologue(const double* __restrict__ u1, double* __restrict__ ws,
-                           const int32_t* __restrict__ perm, int64_t N, int r,
-                           const int32_t* __restrict__ zero_rows, int nzero, int kp,
-                           int32_t* __restrict__ clear, int nclear) {
-    const int64_t tot = N * r;
+// Gathers the input into the workspace's input rows (leaf by leaf in tree
+// order, padding rows zero) in FP64 and, for FP32 operators, in FP32; clears
+// the y-hat rows that are accumulated atomically (in the workspace of the
+// far field); clears `nclear` ints (the flow kernel's counters).
+__global__ void k_prologue(const double* __restrict__ u1, double* __restrict__ ws, float* __restrict__ ws32,
+                           const int32_t* __restrict__ gsrc, int64_t nrows_in, int64_t N, int r,
+                           const int32_t* __restrict__ zero_rows, int nzero, int kp, int32_t* __restrict__ clear,
+                           int nclear) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t tot = nrows_in * r;
     for (int64_t idx = i0; idx < tot; idx += stride) {
         const int64_t q = idx / r, c = idx - q * r;
-        ws[idx] = u1[c * N + perm[q]];
+        const int32_t src = gsrc[q];
+        const double v = src >= 0 ? u1[c * N + src] : 0.0;
+        ws[idx] = v;
+        if (ws32) ws32[idx] = (float)v;
     }
     const int64_t per = (int64_t)kp * r;
     const int64_t totz = (int64_t)nzero * per;
     for (int64_t idx = i0; idx < totz; idx += stride) {
         const int64_t z = idx / per, j = idx - z * per;
-        ws[(int64_t)zero_rows[z] * r + j] = 0.0;
+        if (ws32) ws32[(int64_t)zero_rows[z] * r + j] = 0.0f;
+        else ws[(int64_t)zero_rows[z] * r + j] = 0.0;
     }
     for (int64_t idx = i0; idx < nclear; idx += stride) clear[idx] = 0;
 }
 
-// Shared-memory stages of the segment kernel for r <= rt right-hand sides.
-int stages_for(int rt) { return rt >= 32 ? 2 : 3; }
+// Shared-memory stages of the segment kernel for r <= rt right-hand sides: two
+// 32 KB stages let three CTAs share an SM at small r (measured faster than three
+// stages with two CTAs).
+int stages_for(int rt) { return 2 + 0 * rt; }
 
 int rt_for(int r) {
     int rt = 1;
@@ -574,9 +654,9 @@ int upload_vec(const std::vector<T>& v, T** d) {
 }
 
 // Launches the gather kernel and every pass (level-wise) or the flow kernel
-// on workspace `ws`.
+// on workspaces `ws` (FP64) and `ws32` (FP32 operators only).
 int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream_t s, double* ws,
-                  bool flow, std::vector<cudaEvent_t>* marks,
+                  float* ws32, bool flow, std::vector<cudaEvent_t>* marks,
                   std::vector<cudaEvent_t>* pool) {
     const int rt = rt_for(r);
     const size_t smem = pass_smem_bytes(op, rt);
@@ -599,16 +679,17 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
         const std::vector<int32_t>& zr = flow ? op->fzero_rows : op->zero_rows;
         const int32_t* d_zr = flow ? op->d_fzero_rows : op->d_zero_rows;
         const int nclear = flow ? 3 * op->nc + 1 : 0;
-        const int64_t work = std::max<int64_t>({N * r, (int64_t)zr.size() * op->kp * r, (int64_t)nclear});
+        const int64_t work = std::max<int64_t>({op->row_xhat * r, (int64_t)zr.size() * op->kp * r, (int64_t)nclear});
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 4096));
-        k_prologue<<<grid, 256, 0, s>>>(u1, ws, op->d_perm, N, r, d_zr, (int)zr.size(), op->kp,
-                                        op->d_fcnt, nclear);
+        k_prologue<<<grid, 256, 0, s>>>(u1, ws, ws32, op->d_gather_src, op->row_xhat, N, r, d_zr, (int)zr.size(),
+                                        op->kp, op->d_fcnt, nclear);
         H2_CUDA_TRY(cudaGetLastError());
     }
     H2_CUDA_TRY(mark());
     KArgs a{};
     a.arena = op->d_arena;
     a.ws = ws;
+    a.ws32 = ws32;
     a.u2 = u2;
     a.perm = op->d_perm;
     a.err = op->d_err;
@@ -644,8 +725,8 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
 
 size_t pass_smem_bytes(const h2_handle* op, int rt) {
     const size_t S = (size_t)stages_for(rt);
-    return S * op->stage_bytes + S * sizeof(double) * kMaxChunkCols * rt + sizeof(double) * kConsumers * rt +
-           sizeof(uint64_t) * (2 * S + 1);
+    return S * op->stage_bytes + S * xin_bytes(rt) +
+           (size_t)red_buffers(rt) * sizeof(double) * kConsumers * rt + sizeof(uint64_t) * (2 * S + 1);
 }
 
 // Resident CTAs and per-CTA rates of the dataflow kernel on the current
@@ -675,7 +756,46 @@ int flow_model(h2_handle* op, FlowModel& fm) {
     return H2_OK;
 }
 
+// Checks, on the host, the invariants the bulk copies rely on (16-byte aligned
+// sources, destinations and sizes; chunks within one stage; input rows on
+// 4-row boundaries), so that a plan that violates them is rejected before any
+// kernel sees it.
+static int validate_chunks(const h2_handle* op, const std::vector<Segment>* segs, const std::vector<Chunk>& chunks,
+                           const std::vector<Piece>& pieces) {
+    for (const Chunk& c : chunks) {
+        if (c.src % 16 || c.bytes % 16 || c.bytes <= 0 || c.bytes > op->stage_bytes || c.npieces < 1 ||
+            c.npieces > H2_MAX_CHUNK_PIECES || c.ncols < 1 || c.ncols > kMaxChunkCols ||
+            c.src + c.bytes > op->arena_bytes || (size_t)c.piece0 + c.npieces > pieces.size())
+            return H2_ERR_INVALID_ARG;
+        int cols = 0;
+        for (int q = 0; q < c.npieces; ++q) {
+            const Piece& p = pieces[(size_t)c.piece0 + q];
+            if (p.in_row % 4 || p.in_row < 0 || p.smem_off % 16 || p.smem_off >= c.bytes ||
+                (int64_t)p.in_row + p.ncols > op->ws_rows - 4)
+                return H2_ERR_INVALID_ARG;
+            cols += p.ncols;
+        }
+        if (cols != c.ncols || pieces[c.piece0].in_row != c.in_row0 || pieces[c.piece0].type != c.type0)
+            return H2_ERR_INVALID_ARG;
+    }
+    if (segs)
+        for (const Segment& sg : *segs)
+            if (sg.nchunks < 1 || sg.nrows < 1 || sg.nrows > H2_MAX_LEAF || (size_t)sg.chunk0 + sg.nchunks > chunks.size())
+                return H2_ERR_INVALID_ARG;
+    return H2_OK;
+}
+
 int upload_plan(h2_handle* op) {
+    for (const Pass& p : op->passes) {
+        if (validate_chunks(op, &p.seg, p.chunk, p.piece) != H2_OK) {
+            set_last_error("h2_assemble: internal plan check failed (bulk-copy alignment or chunk limits)");
+            return H2_ERR_INVALID_ARG;
+        }
+    }
+    if (op->use_flow && validate_chunks(op, nullptr, op->fchunk, op->fpiece) != H2_OK) {
+        set_last_error("h2_assemble: internal plan check failed (dataflow chunks)");
+        return H2_ERR_INVALID_ARG;
+    }
     int dev = 0, nsm = 0;
     H2_CUDA_TRY(cudaGetDevice(&dev));
     H2_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -698,7 +818,10 @@ int upload_plan(h2_handle* op) {
             return rc;
         H2_CUDA_TRY(cudaMalloc((void**)&op->d_fcnt, sizeof(int32_t) * (3 * (size_t)op->nc + 1)));
     }
+    if ((rc = upload_vec(op->gather_src, &op->d_gather_src))) return rc;
     H2_CUDA_TRY(cudaMalloc((void**)&op->d_ws, sizeof(double) * (size_t)op->ws_rows * op->params.max_rhs));
+    if (op->params.precision == H2_FP32)
+        H2_CUDA_TRY(cudaMalloc((void**)&op->d_ws32, sizeof(float) * (size_t)op->ws_rows * op->params.max_rhs));
     H2_CUDA_TRY(cudaMalloc((void**)&op->d_err, sizeof(int)));
     H2_CUDA_TRY(cudaMemset(op->d_err, 0, sizeof(int)));
     op->n_launches = op->use_flow ? 2 : 1 + (int)op->passes.size();
@@ -740,7 +863,7 @@ int read_profile(h2_handle* op, std::vector<double>& ms, int& ncalls) {
 
 int matvec_device(h2_handle* op, const double* u1, double* u2, int r, cudaStream_t s) {
     std::vector<cudaEvent_t> ev;
-    int rc = launch_matvec(op, u1, u2, r, s, op->d_ws, op->use_flow != 0,
+    int rc = launch_matvec(op, u1, u2, r, s, op->d_ws, op->d_ws32, op->use_flow != 0,
                            op->prof_enabled ? &ev : nullptr, &op->prof_pool);
     if (op->prof_enabled) op->prof_calls.push_back(std::move(ev));
     return rc;
@@ -816,22 +939,17 @@ extern "C" int h2_matvec_noalloc(h2_handle* op, const double* u1, double* u2, in
     const char *a = (const char*)u1, *b = (const char*)u2;
     if (a < b + bytes && b < a + bytes) return H2_ERR_INVALID_ARG;
     if (!device_pointer(u1) || !device_pointer(u2)) return H2_ERR_INVALID_ARG;
-    if ((size_t)op->ws_rows * (size_t)r > H2_STATIC_WS_DOUBLES) {
-        set_last_error("h2_matvec_noalloc: workspace rows x r exceeds the fixed scratch of 4194304 doubles");
+    // FP64 workspace, then (FP32 operators) the FP32 workspace at a 256-byte boundary
+    const size_t n64 = (size_t)op->ws_rows * (size_t)r;
+    const size_t off32 = (n64 + 31) / 32 * 32;
+    const size_t need = op->params.precision == H2_FP32 ? off32 + (n64 + 1) / 2 : n64;
+    if (need > H2_STATIC_WS_DOUBLES) {
+        set_last_error("h2_matvec_noalloc: the workspace of this operator and r exceeds the fixed 32 MiB scratch");
         return H2_ERR_SCRATCH_LIMIT;
     }
     double* ws = nullptr;
     int rc = static_workspace(&ws);
     if (rc != H2_OK) return rc;
-    return launch_matvec(op, u1, u2, r, (cudaStream_t)cuda_stream, ws, false, nullptr, nullptr);
+    float* ws32 = op->params.precision == H2_FP32 ? reinterpret_cast<float*>(ws + off32) : nullptr;
+    return launch_matvec(op, u1, u2, r, (cudaStream_t)cuda_stream, ws, ws32, false, nullptr, nullptr);
 }
-
-#ifdef H2_TRACE
-// Copies the first n segment records of the last traced flow launch to host.
-extern "C" int h2_trace_read(long long* out, int n) {
-    if (cudaDeviceSynchronize() != cudaSuccess) return H2_ERR_CUDA;
-    if (cudaMemcpyFromSymbol(out, h2::g_h2_trace, sizeof(long long) * 5 * (size_t)n) != cudaSuccess)
-        return H2_ERR_CUDA;
-    return H2_OK;
-}
-#endif

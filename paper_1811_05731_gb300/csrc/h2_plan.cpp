@@ -57,6 +57,7 @@ void emit_pass(h2_handle* op, const char* name, int32_t kind, std::vector<SegSpe
         sg.out_row = s.out_row;
         sg.nrows = s.nrows;
         sg.mode = s.mode;
+        sg.out_f32 = op->params.precision == H2_FP32 && s.mode != SEG_FINAL && s.mode != SEG_FINAL_ADD;
         sg.chunk0 = (int32_t)p.chunk.size();
         Chunk cur{};
         cur.src = -1;
@@ -77,12 +78,15 @@ void emit_pass(h2_handle* op, const char* name, int32_t kind, std::vector<SegSpe
             p.macs += (int64_t)s.nrows * m.ncols;
             if (mbytes <= stage && m.ncols <= H2_MAX_CHUNK_COLS) {
                 if (cur.src >= 0 && ((arena + mbytes - cur.src) > stage ||
-                                     cur_cols + m.ncols > H2_MAX_CHUNK_COLS))
+                                     cur_cols + m.ncols > H2_MAX_CHUNK_COLS ||
+                                     cur.npieces >= H2_MAX_CHUNK_PIECES))
                     close();
                 if (cur.src < 0) {
                     cur.src = arena;
                     cur.piece0 = (int32_t)p.piece.size();
                     cur.npieces = 0;
+                    cur.in_row0 = m.in_row;
+                    cur.type0 = m.type;
                 }
                 Piece pc{};
                 pc.smem_off = (int32_t)(arena - cur.src);
@@ -96,7 +100,7 @@ void emit_pass(h2_handle* op, const char* name, int32_t kind, std::vector<SegSpe
                 cur.bytes = (int32_t)(arena + mbytes - cur.src);
             } else {
                 close();
-                const int step = es == 8 ? 2 : 4;   // keeps every piece a multiple of 16 bytes
+                const int step = 4;   // keeps every piece's input row a multiple of 4
                 int cols = (int)(stage / ((int64_t)s.nrows * es));
                 cols = std::max(step, std::min(cols, H2_MAX_CHUNK_COLS) / step * step);
                 for (int c0 = 0; c0 < m.ncols; c0 += cols) {
@@ -107,6 +111,8 @@ void emit_pass(h2_handle* op, const char* name, int32_t kind, std::vector<SegSpe
                     ch.piece0 = (int32_t)p.piece.size();
                     ch.npieces = 1;
                     ch.ncols = cc;
+                    ch.in_row0 = m.in_row + c0;
+                    ch.type0 = m.type;
                     Piece pc{};
                     pc.smem_off = 0;
                     pc.in_row = m.in_row + c0;
@@ -151,9 +157,22 @@ void build_plan(h2_handle* op) {
         op->need_y[c] = op->is_tgt[c] || (p >= 0 && op->need_y[p]);
     }
 
-    op->row_xhat = (N + 1) / 2 * 2;
+    // input rows: leaf by leaf in tree order, each leaf padded to 4 rows
+    op->leaf_row.assign(nc, -1);
+    op->gather_src.clear();
+    std::vector<int32_t> leaves;
+    for (int c = 0; c < nc; ++c)
+        if (op->child0[c] < 0) leaves.push_back(c);
+    std::sort(leaves.begin(), leaves.end(), [&](int32_t x, int32_t y) { return op->start[x] < op->start[y]; });
+    for (int32_t c : leaves) {
+        op->leaf_row[c] = (int32_t)op->gather_src.size();
+        for (int a = 0; a < op->size[c]; ++a) op->gather_src.push_back(op->perm[op->start[c] + a]);
+        while (op->gather_src.size() % 4) op->gather_src.push_back(-1);
+    }
+    (void)N;
+    op->row_xhat = (int64_t)op->gather_src.size();
     op->row_yhat = op->row_xhat + (int64_t)nc * kp;
-    op->ws_rows = op->row_yhat + (int64_t)nc * kp + 2;
+    op->ws_rows = op->row_yhat + (int64_t)nc * kp + 4;
     auto xrow = [&](int c) { return (int32_t)(op->row_xhat + (int64_t)c * kp); };
     auto yrow = [&](int c) { return (int32_t)(op->row_yhat + (int64_t)c * kp); };
 
@@ -175,7 +194,7 @@ void build_plan(h2_handle* op) {
             s.out_row = xrow(c);
             s.nrows = k;
             s.mode = SEG_STORE;
-            s.mats.push_back({&op->W[c], op->size[c], P, op->start[c]});
+            s.mats.push_back({&op->W[c], op->size[c], P, op->leaf_row[c]});
             s.bytes = (int64_t)k * op->size[c];
             segs.push_back(s);
         }
@@ -255,7 +274,7 @@ void build_plan(h2_handle* op) {
             s.mode = SEG_FINAL;
             for (int32_t b : near_by_t[t]) {
                 const int32_t sc = op->near_s[b];
-                s.mats.push_back({&op->Nb[b], op->size[sc], PIECE_F64, op->start[sc]});
+                s.mats.push_back({&op->Nb[b], op->size[sc], PIECE_F64, op->leaf_row[sc]});
                 s.bytes += 2LL * op->size[t] * op->size[sc];
             }
             segs.push_back(s);
@@ -456,6 +475,10 @@ double build_flow(h2_handle* op, const FlowModel& fm) {
             }
         }
     }
+    // every writer warp of the kernel (one per 32 rows) signals a finished segment
+    std::fill(op->fexpect.begin(), op->fexpect.end(), 0);
+    for (const Item& it : items)
+        if (it.fs.signal >= 0) op->fexpect[it.fs.signal] += (it.fs.s.nrows + 31) / 32;
     for (int32_t i : order) {
         Item& it = items[i];
         it.fs.dep0 = (int32_t)op->fdeps.size();
