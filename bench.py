@@ -41,13 +41,20 @@ FP32_FMA_PER_CLK_SM = 128
 PASS_NAMES = {0: "gather", 1: "up_leaf", 2: "up_transfer", 3: "coupling", 4: "down_transfer",
               5: "leaf_near", 6: "leaf_expand", 7: "flow"}
 
-WORKLOADS = {
-    # name: (mesh builder, m, leaf, eta, r, rhs builder)
-    "cube64": (lambda: synth.cube_surface(64), 4, 64, 2.0, 1,
-               lambda mesh, r: synth.normal_dot_field(mesh, 1811)),
-    "ico3": (lambda: synth.icosphere(3), 3, 32, 2.0, 1,
-             lambda mesh, r: synth.gaussian_rhs(mesh.n_vertices, r, 1811)),
-}
+PRECISIONS = ("fp64", "fp32", "tf32x3", "bf16x3")
+DTYPES = {"fp64": "f64", "fp32": "f32+f64", "tf32x3": "tf32x3+f64", "bf16x3": "bf16x3+f64"}
+# reduced-precision and batched forms timed beside the headline form (same
+# workload, same GPU): (precision, right-hand sides)
+FORMS = [("fp32", 1), ("tf32x3", 1), ("bf16x3", 1), ("fp64", 32), ("fp32", 32), ("tf32x3", 32),
+         ("bf16x3", 32)]
+
+
+def workload_inputs(name: str, r: int):
+    """The named synthetic workload; r > 0 replaces its right-hand sides by r
+    seeded smooth magnetisation states u1 = n . m_c."""
+    w = synth.make_workload(name)
+    u1 = w.u1 if r <= 0 else synth.smooth_states(w.mesh, r, 1811)
+    return w, np.ascontiguousarray(np.atleast_2d(u1), dtype=np.float64)
 
 
 def measured_peaks():
@@ -144,9 +151,8 @@ def cpu_oracle_rate(mesh, m, leaf, eta, u1, budget_s: float):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    build, m, leaf, eta, r, rhs = WORKLOADS[args.workload]
-    mesh = build()
-    u1 = np.atleast_2d(rhs(mesh, r))
+    w, u1 = workload_inputs(args.workload, args.r)
+    mesh, m, leaf, eta = w.mesh, w.m, w.leaf, w.eta
     import oracle
     oracle.build()
     o = oracle.H2Oracle(mesh.xyz, mesh.tri, m, leaf, eta)
@@ -171,86 +177,47 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args, rank, local, world):
-    import torch
-    import paper_1811_05731_gb300 as pkg
-
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    pkg.build()
-    build, m, leaf, eta, r, rhs = WORKLOADS[args.workload]
-    if args.r:
-        r = args.r
-    mesh = build()
-    N = mesh.n_vertices
-    u1_np = np.ascontiguousarray(np.atleast_2d(rhs(mesh, r)), dtype=np.float64)
+def time_form(pkg, torch, g, w, u1_np, precision, schedule, steps, warmup, barrier=None):
+    """Builds the operator of one form and times `steps` matvecs with CUDA
+    events on the launching stream (inputs resident in device memory)."""
     r = u1_np.shape[0]
-    prec = pkg.FP32 if args.precision == "fp32" else pkg.FP64
-    g = pkg.Geometry(mesh.xyz, mesh.tri)
-    op = pkg.Operator(g, m=m, leaf=leaf, eta=eta, precision=prec, max_rhs=r,
-                      schedule=pkg.SCHEDULE_FLOW if args.schedule == "flow" else pkg.SCHEDULE_LEVELS)
-    st = op.stats()
+    op = pkg.Operator(g, m=w.m, leaf=w.leaf, eta=w.eta, precision={"fp64": pkg.FP64, "fp32": pkg.FP32,
+                      "tf32x3": pkg.TF32X3, "bf16x3": pkg.BF16X3}[precision], max_rhs=r,
+                      schedule=pkg.SCHEDULE_FLOW if schedule == "flow" else pkg.SCHEDULE_LEVELS)
     stream = torch.cuda.current_stream()
     sp = int(stream.cuda_stream)
     x = torch.from_numpy(u1_np).cuda()
     y = torch.empty_like(x)
-
-    def step():
+    for _ in range(max(warmup, 3)):
         pkg.h2_matvec(op.handle, x.data_ptr(), y.data_ptr(), r, sp)
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    for _ in range(max(args.warmup, 3)):
-        step()
     torch.cuda.synchronize()
-    # device-timed region (matrices streamed per step exceed the L2 cache)
-    with ClockSampler(local) as clk:
+    if barrier:
         barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-    t_step = e0.elapsed_time(e1) / 1e3 / args.steps
-    if dist is not None:
-        t = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
-    value = N * r * world / t_step
-
-    # end to end through the C ABI with pinned host buffers
-    xh = torch.from_numpy(u1_np).pin_memory()
-    yh = torch.empty_like(xh).pin_memory()
-    for _ in range(2):
-        pkg.h2_matvec(op.handle, xh.data_ptr(), yh.data_ptr(), r, sp)
-    barrier()
     torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        pkg.h2_matvec(op.handle, xh.data_ptr(), yh.data_ptr(), r, sp)
+    for _ in range(steps):
+        pkg.h2_matvec(op.handle, x.data_ptr(), y.data_ptr(), r, sp)
     e1.record(stream)
     torch.cuda.synchronize()
-    t_e2e = e0.elapsed_time(e1) / 1e3 / args.steps
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    if barrier:
+        barrier()
+    status = pkg.h2_device_status(op.handle)
+    if status != 0:
+        raise RuntimeError(f"device-side wait gave up during the benchmark ({status})")
+    return op, x, y, e0.elapsed_time(e1) / 1e3 / steps
 
-    # per-pass CUDA-event timing over a second run of the same K steps
+
+def pass_profile(pkg, op, x, y, r, steps):
+    """Per-launch CUDA-event times of `steps` matvecs (h2_profile_*)."""
     import ctypes
+    import torch
     L = pkg.load()
+    sp = int(torch.cuda.current_stream().cuda_stream)
     L.h2_profile_enable(ctypes.c_void_p(op.handle), 1)
-    for _ in range(args.steps):
-        step()
+    for _ in range(steps):
+        pkg.h2_matvec(op.handle, x.data_ptr(), y.data_ptr(), r, sp)
     cap = 64
     kind = (ctypes.c_int32 * cap)()
     ms = (ctypes.c_double * cap)()
@@ -269,7 +236,69 @@ def run_gpu(args, rank, local, world):
             passes.append({"launch": i, "pass": PASS_NAMES.get(kind[i], str(kind[i])),
                            "ms": ms[i] / ncalls.value, "bytes": byt[i], "macs_per_rhs": macs[i],
                            "grid": grid[i]})
+    return passes
+
+
+def rel_err(y, ref):
+    return float(np.max(np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+
+
+def run_gpu(args, rank, local, world):
+    import torch
+    import paper_1811_05731_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pkg.build()
+    w, u1_np = workload_inputs(args.workload, args.r)
+    mesh = w.mesh
+    N = mesh.n_vertices
+    r = u1_np.shape[0]
+    g = pkg.Geometry(mesh.xyz, mesh.tri)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # headline form: device-resident inputs, K timed steps, clocks sampled meanwhile
+    with ClockSampler(local) as clk:
+        op, x, y, t_step = time_form(pkg, torch, g, w, u1_np, args.precision, args.schedule, args.steps,
+                                     args.warmup, barrier)
+    if dist is not None:
+        t = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    value = N * r * world / t_step
+    st = op.stats()
+    stream = torch.cuda.current_stream()
+    sp = int(stream.cuda_stream)
+
+    # end to end through the C ABI with pinned host buffers (copies in the timed region)
+    xh = torch.from_numpy(u1_np).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        pkg.h2_matvec(op.handle, xh.data_ptr(), yh.data_ptr(), r, sp)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        pkg.h2_matvec(op.handle, xh.data_ptr(), yh.data_ptr(), r, sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = e0.elapsed_time(e1) / 1e3 / args.steps
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+
+    passes = pass_profile(pkg, op, x, y, r, args.steps)
     y_np = y.cpu().numpy()
+    del op
 
     if rank != 0:
         if dist is not None:
@@ -283,32 +312,26 @@ def run_gpu(args, rank, local, world):
     fp64_peak = N_SM * FP64_FMA_PER_CLK_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
     fp32_peak = N_SM * FP32_FMA_PER_CLK_SM * 2 * sm_max * 1e6 / 1e12
     roofline = None
-    # group launches by pass kind; the dominant kind is the one with most time
-    by_kind = {}
-    for p in passes:
-        d = by_kind.setdefault(p["pass"], {"ms": 0.0, "bytes": 0, "macs": 0, "launches": 0})
-        d["ms"] += p["ms"]
-        d["bytes"] += p["bytes"]
-        d["macs"] += p["macs_per_rhs"]
-        d["launches"] += 1
+
     def kname(p):
-        return "k_flow (whole product)" if p["pass"] == "flow" else f"k_pass ({p['pass']})"
+        return "k_seg dataflow (whole product)" if p["pass"] == "flow" else f"k_seg ({p['pass']})"
 
     if passes:
-        dom = max((p for p in passes), key=lambda p: p["ms"])
+        dom = max(passes, key=lambda p: p["ms"])
         t = dom["ms"] / 1e3
         gbs = dom["bytes"] / t / 1e9
         flops = 2.0 * dom["macs_per_rhs"] * r
-        alu_peak = fp64_peak if prec == pkg.FP64 else fp32_peak
+        alu_peak = fp64_peak if args.precision == "fp64" else fp32_peak
         tfl = flops / t / 1e12
         hbm_frac = gbs / hbm
         alu_frac = tfl / alu_peak
         if alu_frac > hbm_frac:
             roofline = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s",
                         "frac": alu_frac, "traffic": None,
-                        "peak_source": f"{'FP64' if prec == pkg.FP64 else 'FP32'} FMA rate: "
-                                       f"{N_SM} SMs x {FP64_FMA_PER_CLK_SM if prec == pkg.FP64 else FP32_FMA_PER_CLK_SM}"
-                                       f" FMA/clk x 2 x {sm_max:.0f} MHz",
+                        "peak_source": f"{'FP64' if args.precision == 'fp64' else 'FP32'} FMA rate derived from "
+                                       f"unit counts: {N_SM} SMs x "
+                                       f"{FP64_FMA_PER_CLK_SM if args.precision == 'fp64' else FP32_FMA_PER_CLK_SM}"
+                                       f" FMA/clk x 2 x {sm_max:.0f} MHz (microbenchmark: 1.257 TFLOP/s FP64)",
                         "kernel": kname(dom), "hbm_gbs": gbs, "hbm_frac_of_measured": hbm_frac}
         else:
             roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
@@ -322,22 +345,50 @@ def run_gpu(args, rank, local, world):
             if key in tr:
                 roofline["traffic"] = tr[key]
 
+    # the oracle (FP64, CPU) for relative errors, one product per r
+    refs = {}
+    oracle_obj = None
+    if not args.no_errors:
+        import oracle
+        oracle.build()
+        oracle_obj = oracle.H2Oracle(mesh.xyz, mesh.tri, w.m, w.leaf, w.eta)
+        refs[r] = oracle_obj.matvec(u1_np)
+
+    forms = []
+    if not args.no_forms and world == 1:
+        for prec, rr in [(args.precision, r)] + [f for f in FORMS if f != (args.precision, r)]:
+            _, u = workload_inputs(args.workload, rr if rr > 1 else args.r)
+            opf, xf, yf, tf = time_form(pkg, torch, g, w, u, prec, args.schedule, min(args.steps, 20), 3)
+            ent = {"precision": prec, "r": int(u.shape[0]), "value": N * u.shape[0] / tf,
+                   "ms_per_step": tf * 1e3, "dtype": DTYPES[prec]}
+            if oracle_obj is not None:
+                if u.shape[0] not in refs:
+                    refs[u.shape[0]] = oracle_obj.matvec(u)
+                ent["rel_err_vs_fp64_oracle"] = rel_err(yf.cpu().numpy(), refs[u.shape[0]])
+            forms.append(ent)
+            del opf
+        fp64_1 = next((f["value"] for f in forms if f["precision"] == "fp64" and f["r"] == 1), None)
+        for f in forms:
+            if fp64_1:
+                f["speedup_vs_fp64_r1"] = f["value"] / fp64_1
+            same = next((e["value"] for e in forms if e["precision"] == "fp64" and e["r"] == f["r"]), None)
+            if same:
+                f["speedup_vs_fp64_same_r"] = f["value"] / same
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        rate, cores, n, el, setup, y_ref = cpu_oracle_rate(mesh, m, leaf, eta, u1_np, args.cpu_budget)
-        err = float(np.max(np.linalg.norm(y_np - y_ref, axis=1) / np.linalg.norm(y_ref, axis=1)))
+        rate, cores, n, el, setup, y_ref = cpu_oracle_rate(mesh, w.m, w.leaf, w.eta, u1_np, args.cpu_budget)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{n} full H2 matvecs of the same workload in {el:.1f} s (oracle setup "
-                         f"{setup:.1f} s not timed)",
-               "rel_err_gpu_vs_oracle": err}
+                         f"{setup:.1f} s not timed)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == pkg.FP64 else "f32+f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
         "data": "synthetic",
-        "config": {"workload": args.workload, "N": N, "triangles": mesh.n_triangles, "m": m,
-                   "leaf": leaf, "eta": eta, "r": r, "precision": args.precision,
+        "config": {"workload": args.workload, "N": N, "triangles": mesh.n_triangles, "m": w.m,
+                   "leaf": w.leaf, "eta": w.eta, "r": r, "precision": args.precision,
                    "schedule": args.schedule,
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2: {st['bytes_streamed'] / 1e6:.0f} MB of matrices "
@@ -346,8 +397,10 @@ def run_gpu(args, rank, local, world):
         "e2e": {"value": N * r * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * N * r,
                 "d2h_bytes_per_step": 8 * N * r},
         "gpu_launches": st["n_launches_matvec"] * args.steps,
+        "rel_err_vs_fp64_oracle": rel_err(y_np, refs[r]) if r in refs else None,
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "forms": forms,
         "passes": passes,
         "h2": {k: st[k] for k in ("n_clusters", "n_levels", "n_far_blocks", "n_near_blocks",
                                   "near_entries", "bytes_streamed", "macs_per_rhs",
@@ -364,12 +417,14 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="h2bem", choices=["h2bem", "reference"])
-    ap.add_argument("--workload", default="cube64", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--workload", default="cube64", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
     ap.add_argument("--r", type=int, default=0)
     ap.add_argument("--schedule", default="flow", choices=["flow", "levels"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision and batched forms")
+    ap.add_argument("--no-errors", action="store_true", help="skip the relative errors against the oracle")
     args = ap.parse_args()
     rank, local, world = rank_info()
     if args.impl == "reference":

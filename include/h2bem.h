@@ -56,10 +56,19 @@ typedef enum {
 /* Storage/arithmetic precision of the far field (transfer, coupling and leaf
  * bases).  Near blocks, the solid-angle diagonal, the geometry and the final
  * per-node sum are FP64 in every mode.
- *  H2_FP64: everything FP64.
- *  H2_FP32: far-field matrices stored in FP32, FP32 products with FP32
- *           accumulation per block, block sums added in FP64. */
-typedef enum { H2_FP64 = 0, H2_FP32 = 1 } h2_precision;
+ *  H2_FP64:   everything FP64 (CUDA cores).
+ *  H2_FP32:   far-field matrices and vectors (x-hat, y-hat) in FP32, FP32
+ *             products with FP32 accumulation on the CUDA cores.
+ *  H2_TF32X3: as H2_FP32, but the coupling and transfer products run on the
+ *             tensor cores (tcgen05) as three TF32 products per term
+ *             (hi*hi + hi*lo + lo*hi, hi = the value with its 13 low mantissa
+ *             bits cleared, lo = the exact remainder), FP32 accumulation.
+ *  H2_BF16X3: coupling and transfer matrices stored as BF16 pairs hi + lo
+ *             (hi = bf16(a), lo = bf16(a - hi), 4 bytes per entry) and
+ *             multiplied on the tensor cores as hi*hi + hi*lo + lo*hi with the
+ *             vectors split the same way, FP32 accumulation.  Leaf bases FP32.
+ * The reduced forms target a relative error <= 1e-5 against the FP64 form. */
+typedef enum { H2_FP64 = 0, H2_FP32 = 1, H2_TF32X3 = 2, H2_BF16X3 = 3 } h2_precision;
 
 typedef struct {
     int32_t m;              /* Chebyshev points per axis, 1..5 (k = m^3 <= 125)       */

@@ -11,6 +11,8 @@ from .build import lib_path
 
 FP64 = 0
 FP32 = 1
+TF32X3 = 2
+BF16X3 = 3
 SCHEDULE_FLOW = 0
 SCHEDULE_LEVELS = 1
 

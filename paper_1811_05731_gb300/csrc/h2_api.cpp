@@ -121,7 +121,7 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
     else h2_default_params(&p);
     if (p.m < 1 || p.m > H2_MAX_M || p.leaf < 1 || p.leaf > H2_MAX_LEAF || !(p.eta > 0.0) ||
         !(p.box_inflation > 0.0) || p.box_inflation > 1.0 || p.max_rhs < 1 || p.max_rhs > H2_MAX_RHS ||
-        (p.precision != H2_FP64 && p.precision != H2_FP32) ||
+        p.precision < H2_FP64 || p.precision > H2_BF16X3 ||
         (p.schedule != H2_SCHEDULE_FLOW && p.schedule != H2_SCHEDULE_LEVELS))
         return H2_ERR_INVALID_ARG;
     for (int i = 0; i < 3; ++i)

@@ -13,6 +13,7 @@
 // Sign convention of the double-layer term: K_ij = (1/4pi) oint phi_j(y)
 // n_y . (xi_i - y) / |xi_i - y|^3 dS_y, under which a constant u1 gives
 // u2 = -u1 (the row sums of M are -1).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -126,6 +127,25 @@ __device__ __forceinline__ void store(unsigned char* arena, int64_t off, int64_t
     else reinterpret_cast<double*>(arena + off)[idx] = v;
 }
 
+// Stores entry (i, j) of an nrows-row far-field block in the operator's
+// format `type` (a PieceType): column-major FP64 / FP32, a TF32 tensor tile
+// (FP32 values), or a BF16 hi + lo tensor tile (hi = bf16(v), lo = bf16(v - hi)).
+__device__ __forceinline__ void store_block(unsigned char* arena, int64_t off, int nrows, int i, int j, double v,
+                                            int type) {
+    if (type == PIECE_F64) {
+        reinterpret_cast<double*>(arena + off)[(int64_t)j * nrows + i] = v;
+    } else if (type == PIECE_F32) {
+        reinterpret_cast<float*>(arena + off)[(int64_t)j * nrows + i] = (float)v;
+    } else if (type == PIECE_TF32) {
+        *reinterpret_cast<float*>(arena + off + tc_offset(type, tc_rows(nrows), i, j, 0)) = (float)v;
+    } else {
+        const __nv_bfloat16 hi = __double2bfloat16(v);
+        const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+        *reinterpret_cast<__nv_bfloat16*>(arena + off + tc_offset(type, tc_rows(nrows), i, j, 0)) = hi;
+        *reinterpret_cast<__nv_bfloat16*>(arena + off + tc_offset(type, tc_rows(nrows), i, j, 1)) = lo;
+    }
+}
+
 struct BasisItem {
     double box[6];
     int64_t off;
@@ -206,7 +226,7 @@ struct TransferItem {
 // E_c(nu', nu) = L^parent_nu(x^c_nu').  Up layout (nu, nu') at nu'*k + nu,
 // down layout (nu', nu) at nu*k + nu'.
 __global__ void k_transfer(const TransferItem* __restrict__ items, int m, unsigned char* arena,
-                           int f32) {
+                           int type) {
     const TransferItem& it = items[blockIdx.x];
     const int k = m * m * m;
     const int nu = threadIdx.x;
@@ -219,8 +239,8 @@ __global__ void k_transfer(const TransferItem* __restrict__ items, int m, unsign
         const int a2 = np / (m * m), b2 = (np / m) % m, c2 = np % m;
         const double v = lagr(cp.p[0], m, a, cc.p[0][a2]) * lagr(cp.p[1], m, b, cc.p[1][b2]) *
                          lagr(cp.p[2], m, c, cc.p[2][c2]);
-        if (it.off_up >= 0) store(arena, it.off_up, (int64_t)np * k + nu, v, f32);
-        if (it.off_down >= 0) store(arena, it.off_down, (int64_t)nu * k + np, v, f32);
+        if (it.off_up >= 0) store_block(arena, it.off_up, k, nu, np, v, type);
+        if (it.off_down >= 0) store_block(arena, it.off_down, k, np, nu, v, type);
     }
 }
 
@@ -231,7 +251,7 @@ struct CouplingItem {
 
 // S_ts (k x k column-major: (nu, mu) at mu*k + nu).
 __global__ void k_coupling(const CouplingItem* __restrict__ items, int m,
-                           const double* __restrict__ box, unsigned char* arena, int f32) {
+                           const double* __restrict__ box, unsigned char* arena, int type) {
     const CouplingItem it = items[blockIdx.x];
     const int k = m * m * m;
     __shared__ double pt[3][H2_MAX_K], ps[3][H2_MAX_K];
@@ -252,7 +272,7 @@ __global__ void k_coupling(const CouplingItem* __restrict__ items, int m,
         const double dx = pt[0][nu] - ps[0][mu], dy = pt[1][nu] - ps[1][mu],
                      dz = pt[2][nu] - ps[2][mu];
         const double v = 1.0 / (4.0 * kPi * sqrt(dx * dx + dy * dy + dz * dz));
-        store(arena, it.off, idx, v, f32);
+        store_block(arena, it.off, k, nu, mu, v, type);
     }
 }
 
@@ -382,7 +402,11 @@ int geometry_device_setup(h2_handle* g, cudaStream_t s) {
 int assemble_device(h2_handle* op, cudaStream_t s) {
     const h2_handle* g = op->geom;
     const int m = op->m, k = op->k;
-    const int f32 = op->params.precision == H2_FP32 ? 1 : 0;
+    // leaf bases: FP64 or FP32 column-major; coupling and transfer blocks in
+    // the operator's far-field format
+    const int prec = op->params.precision;
+    const int f32 = prec == H2_FP64 ? 0 : 1;
+    const int tt = prec == H2_FP64 ? PIECE_F64 : prec == H2_FP32 ? PIECE_F32 : prec == H2_TF32X3 ? PIECE_TF32 : PIECE_BF16X3;
     int rc;
 
     H2_CUDA_TRY(cudaMalloc((void**)&op->d_arena, (size_t)std::max<int64_t>(op->arena_bytes, 16)));
@@ -439,7 +463,7 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
     TransferItem* d_ti = nullptr;
     if ((rc = upload(ti, &d_ti, s))) { cleanup(); return rc; }
     tmp.push_back(d_ti);
-    if (!ti.empty()) k_transfer<<<(unsigned)ti.size(), kb, 0, s>>>(d_ti, m, op->d_arena, f32);
+    if (!ti.empty()) k_transfer<<<(unsigned)ti.size(), kb, 0, s>>>(d_ti, m, op->d_arena, tt);
 
     // coupling
     std::vector<CouplingItem> ci(op->far_t.size());
@@ -447,7 +471,7 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
     CouplingItem* d_ci = nullptr;
     if ((rc = upload(ci, &d_ci, s))) { cleanup(); return rc; }
     tmp.push_back(d_ci);
-    if (!ci.empty()) k_coupling<<<(unsigned)ci.size(), 256, 0, s>>>(d_ci, m, op->d_box, op->d_arena, f32);
+    if (!ci.empty()) k_coupling<<<(unsigned)ci.size(), 256, 0, s>>>(d_ci, m, op->d_box, op->d_arena, tt);
 
     // near field: per source leaf, the triangles around its nodes
     std::vector<int32_t> leaf_pos(op->nc, -1);

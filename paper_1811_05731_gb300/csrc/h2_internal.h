@@ -37,7 +37,35 @@ enum SegMode : int32_t {
     SEG_FINAL_ADD = 4,  // u2[c * N + perm[out_row + i]] += sum (after the near field)
 };
 
-enum PieceType : int32_t { PIECE_F64 = 0, PIECE_F32 = 1 };
+// How a stored matrix is laid out and multiplied.  PIECE_F64 / PIECE_F32:
+// column-major, CUDA cores.  PIECE_TF32 / PIECE_BF16X3: a tensor-core tile
+// (see tc_offset), multiplied by tcgen05.
+enum PieceType : int32_t { PIECE_F64 = 0, PIECE_F32 = 1, PIECE_TF32 = 2, PIECE_BF16X3 = 3 };
+
+inline __host__ __device__ bool piece_tc(int type) { return type >= PIECE_TF32; }
+// Rows of a tensor-core tile (the MMA's M) for a block of `nrows` rows.
+inline __host__ __device__ int tc_rows(int nrows) { return nrows <= 64 ? 64 : 128; }
+// Columns (the MMA's K) multiplied by one tcgen05.mma.
+inline __host__ __device__ int tc_kstep(int type) { return type == PIECE_TF32 ? 8 : 16; }
+// Consumer warps that write a finished segment (and, in the dataflow form,
+// each signal its region once): one per 32 rows on the CUDA cores; the four
+// warps that own the TMEM lane quarters for tensor-core segments.
+inline __host__ __device__ int segment_writers(int nrows, bool tc) { return tc ? 4 : (nrows + 31) / 32; }
+// Byte offset of entry (i, j) in a tensor-core tile of Mp rows.  The tile is a
+// sequence of K slabs (tc_kstep columns each, all rows); a slab holds two
+// "core matrices" along K, each Mp/8 groups of 8 rows x 16 bytes, so that
+// shared-memory descriptors with a K-direction core stride (LBO) of 16*Mp
+// bytes and a row-group stride (SBO) of 128 bytes address it.  BF16X3 slabs
+// hold the hi cores followed by the lo cores (`lo` selects them).
+inline __host__ __device__ int64_t tc_offset(int type, int Mp, int i, int j, int lo) {
+    const int ks = tc_kstep(type);
+    const int es = type == PIECE_TF32 ? 4 : 2;
+    const int per = 16 / es;
+    const int s = j / ks, jj = j % ks;
+    const int64_t slab = (int64_t)ks * Mp * 4;   // both types: 4 bytes per entry
+    return s * slab + (int64_t)lo * 2 * 16 * Mp + (jj / per) * 16 * Mp + (i / 8) * 128 + (i % 8) * 16 +
+           (jj % per) * es;
+}
 
 // A contiguous, 16-byte aligned byte range of the arena that one bulk copy
 // brings into one shared-memory stage.  It holds whole small blocks or a

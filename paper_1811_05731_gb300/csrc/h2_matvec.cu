@@ -24,6 +24,7 @@
 // one right-hand side).  FP32 pieces (far field of an FP32 operator) multiply
 // and accumulate in FP32 within a piece and add the piece's sum to the FP64
 // accumulator; the workspace and u2 are FP64.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -100,6 +101,8 @@ struct StageDesc {
     int32_t f32;       // 1 if the chunk's matrices and inputs are FP32
     int32_t out_row, nrows, mode, signal;
     int32_t out_f32;   // 1 if the segment's output rows are FP32
+    int32_t ptype;     // PieceType of the chunk's matrices
+    int32_t cbytes;    // bytes of the chunk's matrices in the stage
 };
 
 // One matrix of a staged chunk, as the consumers read it.
@@ -129,6 +132,9 @@ struct KArgs {
     int r;
     int stages;
     int stage_bytes;
+    int tc;                    // the operator has tensor-core segments
+    int tc_alo_bytes;          // shared memory for the TF32 lo parts of a chunk
+    int tc_b_bytes;            // shared memory for each of the B hi / lo operands
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -298,6 +304,52 @@ __device__ __forceinline__ void write_segment(const StageDesc& D, const double* 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core (tcgen05) products of far-field chunks.
+//
+// A chunk of coupling or transfer blocks arrives as tensor tiles (see
+// tc_offset).  The consumer warps split the operands into hi and lo parts in
+// shared memory (TF32: hi = the FP32 value with its 13 low mantissa bits
+// cleared, written back in place, exactly representable in TF32; lo = the
+// exact remainder.  BF16: the tiles already hold hi and lo), build the
+// K-major B operand (the chunk's input vectors, N = r padded to the MMA's
+// granularity, hi and lo), and one thread issues, per K step, the three
+// products hi*hi + hi*lo + lo*hi into an FP32 accumulator in tensor memory
+// (M = 64 or 128 rows).  The accumulator lives across the chunks of a
+// segment; at its end the four warps that own the TMEM lane quarters read it
+// out (row i of an M = 128 tile is lane i; rows 16q..16q+15 of an M = 64 tile
+// are lanes 32q..32q+15) and write the segment.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    // start address, K-direction core stride (LBO), row-group stride (SBO),
+    // descriptor version 1 (bit 46), no swizzle
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ uint32_t mma_idesc(int type, int M, int N) {
+    const uint32_t fmt = type == PIECE_TF32 ? 2u : 1u;   // TF32 (kind::tf32) or BF16 (kind::f16)
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_issue(int type, uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+    if (type == PIECE_TF32)
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                     "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+                     : "memory");
+    else
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                     "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+                     : "memory");
+}
+__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+// Byte offset of B entry (n, kk) in a K-major operand of Np rows (K slow).
+__device__ __forceinline__ int b_offset(int n, int kk, int Np, int es) {
+    const int per = 16 / es;
+    return (kk / per) * (Np / 8) * 128 + (n / 8) * 128 + (n % 8) * 16 + (kk % per) * es;
+}
+
 // Input buffer of one stage: at most kMaxChunkCols FP64 rows of RT values
 // plus the 16-byte rounding of every piece.
 __host__ __device__ constexpr size_t xin_bytes(int rt) {
@@ -310,9 +362,10 @@ __host__ __device__ constexpr int red_buffers(int rt) { return rt <= 8 ? 2 : 1; 
 
 // Shared-memory layout of the segment kernel (dynamic part):
 //   stages x stage_bytes             matrix chunks (bulk copies)
-//   stages x kMaxChunkCols*RT*8      the chunks' input values
+//   stages x xin_bytes(RT)           the chunks' input values
 //   red_buffers x kConsumers*RT*8    partial sums of the row groups
-//   stages x 2 + 1 mbarriers         full[], empty[], segment barrier
+//   tc_alo_bytes, 2 x tc_b_bytes     tensor-core operands (TF32 lo parts, B hi / lo)
+//   stages x 2 + 3 mbarriers         full[], empty[], segment, operands-ready, products-done
 //
 // Warp specialisation.  The producer warp (the last warp) walks this CTA's
 // chunks: it waits until the consumers released the stage, issues the bulk
@@ -327,7 +380,7 @@ __host__ __device__ constexpr int red_buffers(int rt) { return rt <= 8 ? 2 : 1; 
 // the segment and, in the dataflow form, each signals the segment's region
 // with a release add.  No CTA-wide barrier is taken per chunk and no
 // wait is unbounded.
-template <int RT, bool FLOW>
+template <int RT, bool FLOW, bool TC>
 __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int S = a.stages;
@@ -336,12 +389,26 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
     unsigned char* stage_base = smem;
     unsigned char* xbase = smem + (size_t)S * a.stage_bytes;
     double* red = reinterpret_cast<double*>(xbase + (size_t)S * kXin);
-    uint64_t* full = reinterpret_cast<uint64_t*>(red + NRED * kConsumers * RT);
+    // tensor-core operands: after the partial sums, or over them when there is
+    // a single partial-sum buffer (its readers finish behind a consumer barrier
+    // before the next chunk is prepared)
+    unsigned char* tc_alo = NRED == 1 ? reinterpret_cast<unsigned char*>(red)
+                                      : reinterpret_cast<unsigned char*>(red + NRED * kConsumers * RT);
+    unsigned char* tc_bhi = tc_alo + a.tc_alo_bytes;
+    unsigned char* tc_blo = tc_bhi + a.tc_b_bytes;
+    const size_t red_span = (size_t)NRED * kConsumers * RT * sizeof(double);
+    const size_t tc_span = (size_t)a.tc_alo_bytes + 2 * (size_t)a.tc_b_bytes;
+    uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(red) +
+                                                  (NRED == 1 ? (red_span > tc_span ? red_span : tc_span)
+                                                             : red_span + tc_span));
     uint64_t* empty = full + S;
     uint64_t* segbar = empty + S;
+    uint64_t* cbar = segbar + 1;     // consumers: tensor operands ready
+    uint64_t* mmabar = cbar + 1;     // tensor-core products of a chunk done
     __shared__ StageDesc sd[kMaxStages];
     __shared__ SPiece spc[kMaxStages][H2_MAX_CHUNK_PIECES];
     __shared__ int abort_flag;
+    __shared__ uint32_t tmem_base;
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -351,9 +418,18 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
             mbar_init(&empty[s], kConsumers);
         }
         mbar_init(segbar, kConsumers);
+        mbar_init(cbar, kConsumers);
+        mbar_init(mmabar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (TC && tid < 32) {   // 32 TMEM columns: one FP32 accumulator of up to 128 rows x 32 RHS
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_addr(&tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     volatile int* abortp = &abort_flag;
     int issued = 0;   // producer: chunks whose copy was issued
 
@@ -409,7 +485,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
             const int cnp = __shfl_sync(~0u, myc.npieces, src_lane);
             const int cncols = __shfl_sync(~0u, myc.ncols, src_lane);
             const int cin0 = __shfl_sync(~0u, myc.in_row0, src_lane);
-            const bool f32 = __shfl_sync(~0u, myc.type0, src_lane) == PIECE_F32;
+            const int ctype = __shfl_sync(~0u, myc.type0, src_lane);
+            const bool f32 = ctype != PIECE_F64;   // FP32 inputs (FP32 workspace)
             if (lane == 0) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 tma_load(stage_base + (size_t)st * a.stage_bytes, a.arena + csrc, (uint32_t)cbytes, &full[st]);
@@ -471,6 +548,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                 D.nrows = F.s.nrows;
                 D.mode = F.s.mode;
                 D.out_f32 = F.s.out_f32;
+                D.ptype = ctype;
+                D.cbytes = cbytes;
                 D.signal = F.signal;
                 sd[st] = D;
                 mbar_arrive(&full[st]);
@@ -483,7 +562,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
         double acc[RT];
 #pragma unroll
         for (int c = 0; c < RT; ++c) acc[c] = 0.0;
-        uint32_t segphase = 0;
+        uint32_t segphase = 0, cphase = 0, mphase = 0;
+        bool tc_fresh = true;   // thread 0: the next product starts a segment's accumulator
         for (int i = 0;; ++i) {
             const int st = i % S;
             if (!mbar_wait_or_abort(&full[st], (uint32_t)(i / S) & 1u, abortp)) {
@@ -493,6 +573,131 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
             }
             const StageDesc D = sd[st];
             if (D.seg < 0) break;
+            if (TC && piece_tc(D.ptype)) {
+                // ---------- tensor-core chunk ----------
+                unsigned char* stg = stage_base + (size_t)st * a.stage_bytes;
+                const unsigned char* xin = xbase + (size_t)st * kXin;
+                const int type = D.ptype;
+                const int Mp = tc_rows(D.nrows);
+                const int Np = Mp == 64 ? (r + 7) / 8 * 8 : (r + 15) / 16 * 16;
+                const int ks = tc_kstep(type);
+                const int bes = type == PIECE_TF32 ? 4 : 2;
+                if (type == PIECE_TF32) {   // A = hi (in place) + lo
+                    float4* A4 = reinterpret_cast<float4*>(stg);
+                    float4* L4 = reinterpret_cast<float4*>(tc_alo);
+                    for (int q = tid; q < D.cbytes / 16; q += kConsumers) {
+                        const float4 v = A4[q];
+                        const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+                        A4[q] = h;
+                        L4[q] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+                    }
+                }
+                // B operand: rows n < Np (right-hand sides), K = the pieces' input rows
+                // (each piece padded to whole K steps with zeros)
+                int ktot = 0;
+                for (int p = 0; p < D.npieces; ++p) ktot += (spc[st][p].ncols + ks - 1) / ks * ks;
+                for (int idx = tid; idx < ktot * Np; idx += kConsumers) {
+                    const int kk = idx / Np, n = idx - kk * Np;
+                    int p = 0, kb = 0;
+                    int kp0 = (spc[st][0].ncols + ks - 1) / ks * ks;
+                    while (kk >= kb + kp0) {
+                        kb += kp0;
+                        ++p;
+                        kp0 = (spc[st][p].ncols + ks - 1) / ks * ks;
+                    }
+                    const SPiece P = spc[st][p];
+                    const int j = kk - kb;
+                    const float x = (j < P.ncols && n < r)
+                                        ? reinterpret_cast<const float*>(xin + P.xoff)[j * r + n]
+                                        : 0.0f;
+                    const int off = b_offset(n, kk, Np, bes);
+                    if (type == PIECE_TF32) {
+                        const float h = tf32_hi(x);
+                        *reinterpret_cast<float*>(tc_bhi + off) = h;
+                        *reinterpret_cast<float*>(tc_blo + off) = x - h;
+                    } else {
+                        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                        *reinterpret_cast<__nv_bfloat16*>(tc_bhi + off) = h;
+                        *reinterpret_cast<__nv_bfloat16*>(tc_blo + off) = __float2bfloat16_rn(x - __bfloat162float(h));
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(cbar);
+                if (!mbar_wait_or_abort(cbar, cphase++ & 1u, abortp)) {
+                    atomicExch(a.err, 1);
+                    abort_flag = 1;
+                    break;
+                }
+                if (tid == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t idesc = mma_idesc(type, Mp, Np);
+                    const uint32_t lboA = 16u * Mp, lboB = (uint32_t)(Np / 8) * 128u;
+                    const int bper = 16 / bes;
+                    int kb = 0;
+                    for (int p = 0; p < D.npieces; ++p) {
+                        const SPiece P = spc[st][p];
+                        const int nst = (P.ncols + ks - 1) / ks;
+                        for (int q = 0; q < nst; ++q) {
+                            const uint32_t aoff = (uint32_t)P.smem_off + (uint32_t)(q * ks * Mp * 4);
+                            const uint32_t boff = (uint32_t)((kb + q * ks) / bper) * lboB;
+                            const uint64_t ahi = smem_desc(smem_addr(stg) + aoff, lboA, 128);
+                            const uint64_t alo = type == PIECE_TF32
+                                                     ? smem_desc(smem_addr(tc_alo) + aoff, lboA, 128)
+                                                     : smem_desc(smem_addr(stg) + aoff + 32u * Mp, lboA, 128);
+                            const uint64_t bhi = smem_desc(smem_addr(tc_bhi) + boff, lboB, 128);
+                            const uint64_t blo = smem_desc(smem_addr(tc_blo) + boff, lboB, 128);
+                            mma_issue(type, tmem_base, ahi, bhi, idesc, tc_fresh ? 0u : 1u);
+                            mma_issue(type, tmem_base, ahi, blo, idesc, 1u);
+                            mma_issue(type, tmem_base, alo, bhi, idesc, 1u);
+                            tc_fresh = false;
+                        }
+                        kb += nst * ks;
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_addr(mmabar))
+                                 : "memory");
+                    tc_fresh = D.last != 0;
+                }
+                if (!mbar_wait_or_abort(mmabar, mphase++ & 1u, abortp)) {
+                    atomicExch(a.err, 1);
+                    abort_flag = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                mbar_arrive(&empty[st]);
+                if (D.last && tid < 128) {   // the four lane-quarter warps read the accumulator
+                    const int w = tid >> 5, lane = tid & 31;
+                    const int row = Mp == 128 ? tid : (lane < 16 ? 16 * w + lane : -1);
+                    uint32_t v[32];
+                    const uint32_t taddr = tmem_base + ((uint32_t)(32 * w) << 16);
+#pragma unroll
+                    for (int c0 = 0; c0 < 32; c0 += 8) {
+                        if (c0 < Np)
+                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                         : "=r"(v[c0]), "=r"(v[c0 + 1]), "=r"(v[c0 + 2]), "=r"(v[c0 + 3]),
+                                           "=r"(v[c0 + 4]), "=r"(v[c0 + 5]), "=r"(v[c0 + 6]), "=r"(v[c0 + 7])
+                                         : "r"(taddr + (uint32_t)c0));
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (row >= 0 && row < D.nrows) {
+                        float* dst = a.ws32 + (int64_t)(D.out_row + row) * r;
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            if (c >= r) break;
+                            const float y = __uint_as_float(v[c]);
+                            if (D.mode == SEG_STORE) dst[c] = y;
+                            else if (D.mode == SEG_ADD) dst[c] = __ldcg(dst + c) + y;
+                            else atomicAdd(dst + c, y);
+                        }
+                    }
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    if (FLOW && D.signal >= 0) {
+                        __syncwarp();
+                        if (lane == 0) signal_region(a.cnt + D.signal);
+                    }
+                }
+                continue;
+            }
             const int nrows = D.nrows;
             const int G = kConsumers / nrows;
             const int row = tid % nrows, g = tid / nrows;
@@ -531,11 +736,16 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
             }
         }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     // after an abort, let the producer's copies still in flight land (bounded)
     if (tid == kConsumers && abort_flag) {
         for (int j = issued > S ? issued - S : 0; j < issued; ++j)
             (void)mbar_wait(&full[j % S], (uint32_t)(j / S) & 1u);
+    }
+    if (TC && tid < 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem_base) : "memory");
     }
 }
 
@@ -607,43 +817,50 @@ int ctas_per_sm(F* kernel, size_t smem, int& cached, size_t& cached_smem) {
 
 // Launches `nsm` x (resident CTAs per SM) CTAs (at most one per segment);
 // *launched receives the grid size.
-template <int RT, bool FLOW>
+template <int RT, bool FLOW, bool TC>
 cudaError_t launch_seg_rt(const KArgs& a, int nsm, size_t smem, cudaStream_t s, int* launched) {
     static size_t configured = 0, occ_smem = 0;
     static int occ = 0;
-    cudaError_t e = set_smem(k_seg<RT, FLOW>, smem, configured);
+    cudaError_t e = set_smem(k_seg<RT, FLOW, TC>, smem, configured);
     if (e != cudaSuccess) return e;
-    const int g = std::max(1, std::min(a.nseg, nsm * ctas_per_sm(k_seg<RT, FLOW>, smem, occ, occ_smem)));
+    const int g = std::max(1, std::min(a.nseg, nsm * ctas_per_sm(k_seg<RT, FLOW, TC>, smem, occ, occ_smem)));
     if (launched) *launched = g;
-    k_seg<RT, FLOW><<<g, kBlock, smem, s>>>(a);
+    k_seg<RT, FLOW, TC><<<g, kBlock, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int RT>
+template <int RT, bool TC>
 int seg_occupancy(size_t smem) {
     static size_t configured = 0;
-    if (set_smem(k_seg<RT, true>, smem, configured) != cudaSuccess) {
+    if (set_smem(k_seg<RT, true, TC>, smem, configured) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
     int n = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seg<RT, true>, kBlock, smem) != cudaSuccess || n < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seg<RT, true, TC>, kBlock, smem) != cudaSuccess ||
+        n < 1) {
         cudaGetLastError();
         n = 1;
     }
     return n;
 }
 
+template <bool FLOW, bool TC>
+cudaError_t launch_seg_tc(const KArgs& a, int rt, int nsm, size_t smem, cudaStream_t s, int* launched) {
+    switch (rt) {
+        case 1: return launch_seg_rt<1, FLOW, TC>(a, nsm, smem, s, launched);
+        case 2: return launch_seg_rt<2, FLOW, TC>(a, nsm, smem, s, launched);
+        case 4: return launch_seg_rt<4, FLOW, TC>(a, nsm, smem, s, launched);
+        case 8: return launch_seg_rt<8, FLOW, TC>(a, nsm, smem, s, launched);
+        case 16: return launch_seg_rt<16, FLOW, TC>(a, nsm, smem, s, launched);
+        default: return launch_seg_rt<32, FLOW, TC>(a, nsm, smem, s, launched);
+    }
+}
+
 template <bool FLOW>
 cudaError_t launch_seg(const KArgs& a, int rt, int nsm, size_t smem, cudaStream_t s, int* launched) {
-    switch (rt) {
-        case 1: return launch_seg_rt<1, FLOW>(a, nsm, smem, s, launched);
-        case 2: return launch_seg_rt<2, FLOW>(a, nsm, smem, s, launched);
-        case 4: return launch_seg_rt<4, FLOW>(a, nsm, smem, s, launched);
-        case 8: return launch_seg_rt<8, FLOW>(a, nsm, smem, s, launched);
-        case 16: return launch_seg_rt<16, FLOW>(a, nsm, smem, s, launched);
-        default: return launch_seg_rt<32, FLOW>(a, nsm, smem, s, launched);
-    }
+    return a.tc ? launch_seg_tc<FLOW, true>(a, rt, nsm, smem, s, launched)
+                : launch_seg_tc<FLOW, false>(a, rt, nsm, smem, s, launched);
 }
 
 template <class T>
@@ -651,6 +868,16 @@ int upload_vec(const std::vector<T>& v, T** d) {
     H2_CUDA_TRY(cudaMalloc((void**)d, sizeof(T) * std::max<size_t>(1, v.size())));
     if (!v.empty()) H2_CUDA_TRY(cudaMemcpy(*d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
     return H2_OK;
+}
+
+// Tensor-core operand buffers of an operator: the lo parts of one TF32 chunk,
+// and B (hi and lo) for the largest chunk (stage_bytes / (4 * 64) K rows x 32
+// right-hand sides).
+static int tc_alo_bytes(const h2_handle* op) { return op->params.precision == H2_TF32X3 ? op->stage_bytes : 0; }
+static int tc_b_bytes(const h2_handle* op) {
+    const int p = op->params.precision;
+    if (p != H2_TF32X3 && p != H2_BF16X3) return 0;
+    return op->stage_bytes / (4 * 64) * 32 * (p == H2_TF32X3 ? 4 : 2);
 }
 
 // Launches the gather kernel and every pass (level-wise) or the flow kernel
@@ -697,6 +924,9 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
     a.r = r;
     a.stages = stages_for(rt);
     a.stage_bytes = op->stage_bytes;
+    a.tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
+    a.tc_alo_bytes = tc_alo_bytes(op);
+    a.tc_b_bytes = tc_b_bytes(op);
     if (flow) {
         a.seg = op->d_fseg;
         a.chunk = op->d_fchunk;
@@ -725,8 +955,10 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
 
 size_t pass_smem_bytes(const h2_handle* op, int rt) {
     const size_t S = (size_t)stages_for(rt);
-    return S * op->stage_bytes + S * xin_bytes(rt) +
-           (size_t)red_buffers(rt) * sizeof(double) * kConsumers * rt + sizeof(uint64_t) * (2 * S + 1);
+    const size_t red = (size_t)red_buffers(rt) * sizeof(double) * kConsumers * rt;
+    const size_t tc = (size_t)tc_alo_bytes(op) + 2 * (size_t)tc_b_bytes(op);
+    const size_t mid = red_buffers(rt) == 1 ? std::max(red, tc) : red + tc;
+    return S * op->stage_bytes + S * xin_bytes(rt) + mid + sizeof(uint64_t) * (2 * S + 3);
 }
 
 // Resident CTAs and per-CTA rates of the dataflow kernel on the current
@@ -738,14 +970,15 @@ int flow_model(h2_handle* op, FlowModel& fm) {
     H2_CUDA_TRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
     const int rt = rt_for(op->params.max_rhs);
     const size_t smem = pass_smem_bytes(op, rt);
+    const bool tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
     int occ = 1;
     switch (rt) {
-        case 1: occ = seg_occupancy<1>(smem); break;
-        case 2: occ = seg_occupancy<2>(smem); break;
-        case 4: occ = seg_occupancy<4>(smem); break;
-        case 8: occ = seg_occupancy<8>(smem); break;
-        case 16: occ = seg_occupancy<16>(smem); break;
-        default: occ = seg_occupancy<32>(smem); break;
+        case 1: occ = tc ? seg_occupancy<1, true>(smem) : seg_occupancy<1, false>(smem); break;
+        case 2: occ = tc ? seg_occupancy<2, true>(smem) : seg_occupancy<2, false>(smem); break;
+        case 4: occ = tc ? seg_occupancy<4, true>(smem) : seg_occupancy<4, false>(smem); break;
+        case 8: occ = tc ? seg_occupancy<8, true>(smem) : seg_occupancy<8, false>(smem); break;
+        case 16: occ = tc ? seg_occupancy<16, true>(smem) : seg_occupancy<16, false>(smem); break;
+        default: occ = tc ? seg_occupancy<32, true>(smem) : seg_occupancy<32, false>(smem); break;
     }
     const double ghz = khz > 0 ? khz * 1e-6 : 2.07;
     fm.workers = nsm * occ;
@@ -820,7 +1053,7 @@ int upload_plan(h2_handle* op) {
     }
     if ((rc = upload_vec(op->gather_src, &op->d_gather_src))) return rc;
     H2_CUDA_TRY(cudaMalloc((void**)&op->d_ws, sizeof(double) * (size_t)op->ws_rows * op->params.max_rhs));
-    if (op->params.precision == H2_FP32)
+    if (op->params.precision != H2_FP64)
         H2_CUDA_TRY(cudaMalloc((void**)&op->d_ws32, sizeof(float) * (size_t)op->ws_rows * op->params.max_rhs));
     H2_CUDA_TRY(cudaMalloc((void**)&op->d_err, sizeof(int)));
     H2_CUDA_TRY(cudaMemset(op->d_err, 0, sizeof(int)));
@@ -942,7 +1175,7 @@ extern "C" int h2_matvec_noalloc(h2_handle* op, const double* u1, double* u2, in
     // FP64 workspace, then (FP32 operators) the FP32 workspace at a 256-byte boundary
     const size_t n64 = (size_t)op->ws_rows * (size_t)r;
     const size_t off32 = (n64 + 31) / 32 * 32;
-    const size_t need = op->params.precision == H2_FP32 ? off32 + (n64 + 1) / 2 : n64;
+    const size_t need = op->params.precision != H2_FP64 ? off32 + (n64 + 1) / 2 : n64;
     if (need > H2_STATIC_WS_DOUBLES) {
         set_last_error("h2_matvec_noalloc: the workspace of this operator and r exceeds the fixed 32 MiB scratch");
         return H2_ERR_SCRATCH_LIMIT;
@@ -950,6 +1183,6 @@ extern "C" int h2_matvec_noalloc(h2_handle* op, const double* u1, double* u2, in
     double* ws = nullptr;
     int rc = static_workspace(&ws);
     if (rc != H2_OK) return rc;
-    float* ws32 = op->params.precision == H2_FP32 ? reinterpret_cast<float*>(ws + off32) : nullptr;
+    float* ws32 = op->params.precision != H2_FP64 ? reinterpret_cast<float*>(ws + off32) : nullptr;
     return launch_matvec(op, u1, u2, r, (cudaStream_t)cuda_stream, ws, ws32, false, nullptr, nullptr);
 }

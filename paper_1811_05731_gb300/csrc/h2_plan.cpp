@@ -57,7 +57,7 @@ void emit_pass(h2_handle* op, const char* name, int32_t kind, std::vector<SegSpe
         sg.out_row = s.out_row;
         sg.nrows = s.nrows;
         sg.mode = s.mode;
-        sg.out_f32 = op->params.precision == H2_FP32 && s.mode != SEG_FINAL && s.mode != SEG_FINAL_ADD;
+        sg.out_f32 = op->params.precision != H2_FP64 && s.mode != SEG_FINAL && s.mode != SEG_FINAL_ADD;
         sg.chunk0 = (int32_t)p.chunk.size();
         Chunk cur{};
         cur.src = -1;
@@ -69,14 +69,20 @@ void emit_pass(h2_handle* op, const char* name, int32_t kind, std::vector<SegSpe
             cur_cols = 0;
         };
         for (const MatSpec& m : s.mats) {
+            const bool tc = piece_tc(m.type);
             const int es = esize(m.type);
-            const int64_t mbytes = round16((int64_t)s.nrows * m.ncols * es);
+            // tensor-core tiles: Mp rows x Kp columns, 4 bytes per entry (TF32,
+            // or BF16 hi + lo); column-major blocks otherwise
+            const int Mp = tc_rows(s.nrows);
+            const int kcols = tc ? (m.ncols + tc_kstep(m.type) - 1) / tc_kstep(m.type) * tc_kstep(m.type) : m.ncols;
+            const int64_t col_bytes = tc ? (int64_t)Mp * 4 : (int64_t)s.nrows * es;
+            const int64_t mbytes = round16(col_bytes * kcols);
             m.ref->off = arena;
             m.ref->nrows = s.nrows;
             m.ref->ncols = m.ncols;
             m.ref->type = m.type;
             p.macs += (int64_t)s.nrows * m.ncols;
-            if (mbytes <= stage && m.ncols <= H2_MAX_CHUNK_COLS) {
+            if (mbytes <= stage && kcols <= H2_MAX_CHUNK_COLS) {
                 if (cur.src >= 0 && ((arena + mbytes - cur.src) > stage ||
                                      cur_cols + m.ncols > H2_MAX_CHUNK_COLS ||
                                      cur.npieces >= H2_MAX_CHUNK_PIECES))
@@ -100,23 +106,28 @@ void emit_pass(h2_handle* op, const char* name, int32_t kind, std::vector<SegSpe
                 cur.bytes = (int32_t)(arena + mbytes - cur.src);
             } else {
                 close();
-                const int step = 4;   // keeps every piece's input row a multiple of 4
-                int cols = (int)(stage / ((int64_t)s.nrows * es));
+                // split into column ranges (whole K slabs for tensor-core tiles);
+                // every range starts on a multiple of 4 columns, so its input
+                // rows stay 16-byte aligned
+                const int step = tc ? tc_kstep(m.type) : 4;
+                int cols = (int)(stage / col_bytes);
                 cols = std::max(step, std::min(cols, H2_MAX_CHUNK_COLS) / step * step);
-                for (int c0 = 0; c0 < m.ncols; c0 += cols) {
-                    const int cc = std::min(cols, m.ncols - c0);
+                for (int c0 = 0; c0 < kcols; c0 += cols) {
+                    const int cc = std::min(cols, kcols - c0);
+                    const int real = std::max(0, std::min(cc, m.ncols - c0));   // input columns
+                    if (real == 0) break;
                     Chunk ch{};
-                    ch.src = arena + (int64_t)c0 * s.nrows * es;
-                    ch.bytes = (int32_t)round16((int64_t)cc * s.nrows * es);
+                    ch.src = arena + (int64_t)c0 * col_bytes;
+                    ch.bytes = (int32_t)round16((int64_t)cc * col_bytes);
                     ch.piece0 = (int32_t)p.piece.size();
                     ch.npieces = 1;
-                    ch.ncols = cc;
+                    ch.ncols = real;
                     ch.in_row0 = m.in_row + c0;
                     ch.type0 = m.type;
                     Piece pc{};
                     pc.smem_off = 0;
                     pc.in_row = m.in_row + c0;
-                    pc.ncols = cc;
+                    pc.ncols = real;
                     pc.type = m.type;
                     p.piece.push_back(pc);
                     p.chunk.push_back(ch);
@@ -138,7 +149,10 @@ void build_plan(h2_handle* op) {
     const int nc = op->nc;
     const int k = op->k;
     const int kp = op->kp;
-    const int P = op->params.precision == H2_FP32 ? PIECE_F32 : PIECE_F64;
+    // leaf bases (P) and coupling / transfer matrices (PT) per precision
+    const int prec = op->params.precision;
+    const int P = prec == H2_FP64 ? PIECE_F64 : PIECE_F32;
+    const int PT = prec == H2_FP64 ? PIECE_F64 : prec == H2_FP32 ? PIECE_F32 : prec == H2_TF32X3 ? PIECE_TF32 : PIECE_BF16X3;
     const int64_t N = op->geom->N;
 
     op->is_src.assign(nc, 0);
@@ -210,7 +224,7 @@ void build_plan(h2_handle* op) {
             s.nrows = k;
             s.mode = SEG_STORE;
             for (int ch : {op->child0[c], op->child1[c]})
-                s.mats.push_back({&op->Eup[ch], k, P, xrow(ch)});
+                s.mats.push_back({&op->Eup[ch], k, PT, xrow(ch)});
             s.bytes = 2LL * k * k;
             segs.push_back(s);
         }
@@ -235,7 +249,7 @@ void build_plan(h2_handle* op) {
                 s.mode = SEG_ATOMIC;
                 for (size_t g = g0; g < std::min(by_t[t].size(), g0 + split); ++g) {
                     const int32_t b = by_t[t][g];
-                    s.mats.push_back({&op->S[b], k, P, xrow(op->far_s[b])});
+                    s.mats.push_back({&op->S[b], k, PT, xrow(op->far_s[b])});
                     s.bytes += (int64_t)k * k;
                 }
                 segs.push_back(s);
@@ -255,7 +269,7 @@ void build_plan(h2_handle* op) {
             s.out_row = yrow(c);
             s.nrows = k;
             s.mode = op->is_tgt[c] ? SEG_ADD : SEG_STORE;
-            s.mats.push_back({&op->Edown[c], k, P, yrow(p)});
+            s.mats.push_back({&op->Edown[c], k, PT, yrow(p)});
             s.bytes = (int64_t)k * k;
             segs.push_back(s);
         }
@@ -475,10 +489,12 @@ double build_flow(h2_handle* op, const FlowModel& fm) {
             }
         }
     }
-    // every writer warp of the kernel (one per 32 rows) signals a finished segment
+    // every writer warp of the kernel signals a finished segment
     std::fill(op->fexpect.begin(), op->fexpect.end(), 0);
     for (const Item& it : items)
-        if (it.fs.signal >= 0) op->fexpect[it.fs.signal] += (it.fs.s.nrows + 31) / 32;
+        if (it.fs.signal >= 0)
+            op->fexpect[it.fs.signal] +=
+                segment_writers(it.fs.s.nrows, piece_tc(op->fchunk[it.fs.s.chunk0].type0));
     for (int32_t i : order) {
         Item& it = items[i];
         it.fs.dep0 = (int32_t)op->fdeps.size();
