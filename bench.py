@@ -337,12 +337,18 @@ def run_gpu(args, rank, local, world):
             roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
                         "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
                         "kernel": kname(dom), "alu_tflops": tfl, "alu_frac": alu_frac}
+        # DRAM bytes per launch from an ncu capture (profiles/), used only while
+        # the kernel source is the one that was captured
         tpath = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tpath):
+            import hashlib
             with open(tpath) as f:
                 tr = json.load(f)
+            src = os.path.join(ROOT, "paper_1811_05731_gb300", "csrc", "h2_matvec.cu")
+            with open(src, "rb") as f:
+                sha = hashlib.sha1(f.read()).hexdigest()
             key = f"{args.workload}/{args.precision}/r{r}/{dom['pass']}"
-            if key in tr:
+            if key in tr and tr.get("kernel_source_sha1") == sha:
                 roofline["traffic"] = tr[key]
 
     # the oracle (FP64, CPU) for relative errors, one product per r
