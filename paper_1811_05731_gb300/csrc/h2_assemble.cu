@@ -170,52 +170,105 @@ __global__ void k_leaf_V(const BasisItem* __restrict__ items, int m, const int32
     }
 }
 
+struct LeafTri {
+    int32_t tri;
+    int32_t col[3];     // column of each corner in the source leaf, -1 outside
+};
+
+struct WItem {
+    double box[6];
+    int64_t off;
+    int32_t size;       // nodes of the leaf
+    int32_t tl0, tl1;   // its triangles in the leaf-triangle list
+};
+
 // W_s (k x |s| column-major: (mu, j) at j*k + mu), the integral of phi_j
-// n . grad L_mu over the triangles around node j by a collapsed (Duffy)
+// n . grad L_mu over the triangles around node j, by a collapsed (Duffy)
 // Gauss-Legendre product rule with q points per direction, exact for the
 // polynomial integrand of total degree 3(m-1) when 2q - 1 >= 3m - 2.
-__global__ void k_leaf_W(const BasisItem* __restrict__ items, int m, const int32_t* __restrict__ perm,
+// One CTA per leaf; the leaf's triangles are visited once and every Gauss
+// point contributes to the corners of the triangle that belong to the leaf.
+// Thread mu owns column mu of the leaf's block in shared memory.  At a point
+// y, lane l < 3m of each warp evaluates the Lagrange factor L_{d,j}(y_d)
+// (d = l / m, j = l % m) and lane 3m + l its derivative, in product form with
+// barycentric weights (no divisions), and the threads gather the six factors
+// of L_mu and grad L_mu by shuffles.
+__global__ void k_leaf_W(const WItem* __restrict__ items, const LeafTri* __restrict__ ltri, int m,
                          const double* __restrict__ xyz, const int32_t* __restrict__ tri,
-                         const int64_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
                          const double* __restrict__ gx, const double* __restrict__ gw, int q,
                          unsigned char* arena, int f32) {
-    const BasisItem it = items[blockIdx.x];
+    extern __shared__ double wsm[];
+    const WItem it = items[blockIdx.x];
     const int k = m * m * m;
     const int mu = threadIdx.x;
-    if (mu >= k) return;
+    const int lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < it.size * k; i += blockDim.x) wsm[i] = 0.0;
     Cheb cb;
     cheb_nodes(it.box, m, cb);
+    double wbar[3][H2_MAX_M];
+    for (int d = 0; d < 3; ++d)
+        for (int j = 0; j < m; ++j) {
+            double v = 1.0;
+            for (int l = 0; l < m; ++l)
+                if (l != j) v *= cb.p[d][j] - cb.p[d][l];
+            wbar[d][j] = 1.0 / v;
+        }
+    // this lane's factor: value (role < 3m) or derivative (3m <= role < 6m)
+    const int role = lane < 6 * m ? lane : -1;
+    const int fd = role >= 0 ? (role % (3 * m)) / m : 0;
+    const int fj = role >= 0 ? role % m : 0;
+    const bool fder = role >= 3 * m;
     const int a = mu / (m * m), b = (mu / m) % m, c = mu % m;
-    for (int jl = 0; jl < it.size; ++jl) {
-        const int32_t j = perm[it.start + jl];
-        double acc = 0.0;
-        for (int64_t p = adj_ptr[j]; p < adj_ptr[j + 1]; ++p) {
-            const int32_t* v = tri + 3 * (int64_t)adj[p];
-            const int cj = v[0] == j ? 0 : (v[1] == j ? 1 : 2);
-            const d3 r0 = mk(xyz + 3 * (int64_t)v[0]), r1 = mk(xyz + 3 * (int64_t)v[1]),
-                     r2 = mk(xyz + 3 * (int64_t)v[2]);
-            const d3 e1 = r1 - r0, e2 = r2 - r0;
-            const d3 nn = cross(e1, e2);
-            const double twoA = norm(nn);
-            const d3 n = (1.0 / twoA) * nn;
-            for (int iu = 0; iu < q; ++iu) {
-                const double s = gx[iu];
-                for (int iv = 0; iv < q; ++iv) {
-                    const double t = gx[iv] * (1.0 - s);
-                    const double wt = gw[iu] * gw[iv] * (1.0 - s) * twoA;
-                    const double phi = cj == 0 ? 1.0 - s - t : (cj == 1 ? s : t);
-                    const d3 y = r0 + (s * e1 + t * e2);
-                    const double lx = lagr(cb.p[0], m, a, y.x), ly = lagr(cb.p[1], m, b, y.y),
-                                 lz = lagr(cb.p[2], m, c, y.z);
-                    const double gxv = dlagr(cb.p[0], m, a, y.x) * ly * lz;
-                    const double gyv = lx * dlagr(cb.p[1], m, b, y.y) * lz;
-                    const double gzv = lx * ly * dlagr(cb.p[2], m, c, y.z);
-                    acc += wt * phi * (n.x * gxv + n.y * gyv + n.z * gzv);
+    __syncthreads();
+    for (int t = it.tl0; t < it.tl1; ++t) {
+        const LeafTri lt = ltri[t];
+        const int32_t* v = tri + 3 * (int64_t)lt.tri;
+        const d3 r0 = mk(xyz + 3 * (int64_t)v[0]), r1 = mk(xyz + 3 * (int64_t)v[1]),
+                 r2 = mk(xyz + 3 * (int64_t)v[2]);
+        const d3 e1 = r1 - r0, e2 = r2 - r0;
+        const d3 nn = cross(e1, e2);
+        const double twoA = norm(nn);
+        const d3 n = (1.0 / twoA) * nn;
+        for (int iu = 0; iu < q; ++iu) {
+            const double sc = gx[iu];
+            for (int iv = 0; iv < q; ++iv) {
+                const double tc = gx[iv] * (1.0 - sc);
+                const double wt = gw[iu] * gw[iv] * (1.0 - sc) * twoA;
+                const d3 y = r0 + (sc * e1 + tc * e2);
+                double f = 0.0;
+                if (role >= 0) {
+                    const double x = fd == 0 ? y.x : (fd == 1 ? y.y : y.z);
+                    const double* p = cb.p[fd];
+                    if (!fder) {
+                        f = 1.0;
+                        for (int l = 0; l < m; ++l)
+                            if (l != fj) f *= x - p[l];
+                    } else {
+                        for (int q2 = 0; q2 < m; ++q2) {
+                            if (q2 == fj) continue;
+                            double pr = 1.0;
+                            for (int l = 0; l < m; ++l)
+                                if (l != fj && l != q2) pr *= x - p[l];
+                            f += pr;
+                        }
+                    }
+                    f *= wbar[fd][fj];
+                }
+                const double lx = __shfl_sync(~0u, f, a), ly = __shfl_sync(~0u, f, m + b),
+                             lz = __shfl_sync(~0u, f, 2 * m + c), dx = __shfl_sync(~0u, f, 3 * m + a),
+                             dy = __shfl_sync(~0u, f, 4 * m + b), dz = __shfl_sync(~0u, f, 5 * m + c);
+                if (mu < k) {
+                    const double g = n.x * dx * ly * lz + n.y * lx * dy * lz + n.z * lx * ly * dz;
+                    const double wg = wt * g;
+                    if (lt.col[0] >= 0) wsm[lt.col[0] * k + mu] += wg * (1.0 - sc - tc);
+                    if (lt.col[1] >= 0) wsm[lt.col[1] * k + mu] += wg * sc;
+                    if (lt.col[2] >= 0) wsm[lt.col[2] * k + mu] += wg * tc;
                 }
             }
         }
-        store(arena, it.off, (int64_t)jl * k + mu, acc, f32);
     }
+    if (mu < k)
+        for (int j = 0; j < it.size; ++j) store(arena, it.off, (int64_t)j * k + mu, wsm[j * k + mu], f32);
 }
 
 struct TransferItem {
@@ -335,11 +388,6 @@ struct NearItem {
     int32_t pad;
 };
 
-struct LeafTri {
-    int32_t tri;
-    int32_t col[3];     // column of each corner in the source leaf, -1 outside
-};
-
 // One near block N_ts (|t| x |s| column-major: (a, b) at b*|t| + a) per CTA;
 // thread a owns row a and sums the corner weights of every triangle around
 // the source leaf into the columns of the corners that belong to s.
@@ -421,59 +469,29 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
     };
 
     // leaf bases
-    std::vector<BasisItem> vi, wi;
+    std::vector<BasisItem> vi;
     for (int c = 0; c < op->nc; ++c) {
         BasisItem it{};
         std::memcpy(it.box, &op->box[6 * (size_t)c], sizeof(it.box));
         it.start = op->start[c];
         it.size = op->size[c];
         if (op->V[c].off >= 0) { it.off = op->V[c].off; vi.push_back(it); }
-        if (op->W[c].off >= 0) { it.off = op->W[c].off; wi.push_back(it); }
     }
     std::vector<double> gx, gw;
     const int q = (3 * m) / 2;   // ceil((3m - 1) / 2)
     gauss_legendre_unit(q, gx, gw);
-    BasisItem *d_vi = nullptr, *d_wi = nullptr;
+    BasisItem* d_vi = nullptr;
     double *d_gx = nullptr, *d_gw = nullptr;
-    if ((rc = upload(vi, &d_vi, s)) || (rc = upload(wi, &d_wi, s)) || (rc = upload(gx, &d_gx, s)) ||
-        (rc = upload(gw, &d_gw, s))) {
+    if ((rc = upload(vi, &d_vi, s)) || (rc = upload(gx, &d_gx, s)) || (rc = upload(gw, &d_gw, s))) {
         cleanup();
         return rc;
     }
-    tmp.insert(tmp.end(), {d_vi, d_wi, d_gx, d_gw});
+    tmp.insert(tmp.end(), {d_vi, d_gx, d_gw});
     const int kb = (k + 31) / 32 * 32;
     if (!vi.empty())
         k_leaf_V<<<(unsigned)vi.size(), kb, 0, s>>>(d_vi, m, op->d_perm, g->d_xyz, op->d_arena, f32);
-    if (!wi.empty())
-        k_leaf_W<<<(unsigned)wi.size(), kb, 0, s>>>(d_wi, m, op->d_perm, g->d_xyz, g->d_tri,
-                                                    g->d_adj_ptr, g->d_adj, d_gx, d_gw, q,
-                                                    op->d_arena, f32);
 
-    // transfers
-    std::vector<TransferItem> ti;
-    for (int c = 0; c < op->nc; ++c) {
-        if (op->Eup[c].off < 0 && op->Edown[c].off < 0) continue;
-        TransferItem it{};
-        std::memcpy(it.box_child, &op->box[6 * (size_t)c], sizeof(it.box_child));
-        std::memcpy(it.box_parent, &op->box[6 * (size_t)op->parent[c]], sizeof(it.box_parent));
-        it.off_up = op->Eup[c].off;
-        it.off_down = op->Edown[c].off;
-        ti.push_back(it);
-    }
-    TransferItem* d_ti = nullptr;
-    if ((rc = upload(ti, &d_ti, s))) { cleanup(); return rc; }
-    tmp.push_back(d_ti);
-    if (!ti.empty()) k_transfer<<<(unsigned)ti.size(), kb, 0, s>>>(d_ti, m, op->d_arena, tt);
-
-    // coupling
-    std::vector<CouplingItem> ci(op->far_t.size());
-    for (size_t b = 0; b < ci.size(); ++b) ci[b] = {op->far_t[b], op->far_s[b], op->S[b].off};
-    CouplingItem* d_ci = nullptr;
-    if ((rc = upload(ci, &d_ci, s))) { cleanup(); return rc; }
-    tmp.push_back(d_ci);
-    if (!ci.empty()) k_coupling<<<(unsigned)ci.size(), 256, 0, s>>>(d_ci, m, op->d_box, op->d_arena, tt);
-
-    // near field: per source leaf, the triangles around its nodes
+    // per leaf, the triangles around its nodes (column bases and near field)
     std::vector<int32_t> leaf_pos(op->nc, -1);
     std::vector<LeafTri> ltri;
     std::vector<int32_t> ltr0(op->nc, 0), ltr1(op->nc, 0);
@@ -500,6 +518,58 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
             for (int a = 0; a < op->size[c]; ++a) col_of[op->perm[op->start[c] + a]] = -1;
         }
     }
+    LeafTri* d_lt = nullptr;
+    if ((rc = upload(ltri, &d_lt, s))) { cleanup(); return rc; }
+    tmp.push_back(d_lt);
+    {
+        std::vector<WItem> wj;
+        int maxw = 1;
+        for (int c = 0; c < op->nc; ++c) {
+            if (op->W[c].off < 0) continue;
+            WItem it{};
+            std::memcpy(it.box, &op->box[6 * (size_t)c], sizeof(it.box));
+            it.off = op->W[c].off;
+            it.size = op->size[c];
+            it.tl0 = ltr0[c];
+            it.tl1 = ltr1[c];
+            wj.push_back(it);
+            maxw = std::max(maxw, it.size);
+        }
+        WItem* d_wj = nullptr;
+        if ((rc = upload(wj, &d_wj, s))) { cleanup(); return rc; }
+        tmp.push_back(d_wj);
+        if (!wj.empty()) {
+            const size_t smem = sizeof(double) * (size_t)maxw * k;
+            H2_CUDA_TRY(cudaFuncSetAttribute(k_leaf_W, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_leaf_W<<<(unsigned)wj.size(), kb, smem, s>>>(d_wj, d_lt, m, g->d_xyz, g->d_tri, d_gx, d_gw, q,
+                                                           op->d_arena, f32);
+        }
+    }
+
+    // transfers
+    std::vector<TransferItem> ti;
+    for (int c = 0; c < op->nc; ++c) {
+        if (op->Eup[c].off < 0 && op->Edown[c].off < 0) continue;
+        TransferItem it{};
+        std::memcpy(it.box_child, &op->box[6 * (size_t)c], sizeof(it.box_child));
+        std::memcpy(it.box_parent, &op->box[6 * (size_t)op->parent[c]], sizeof(it.box_parent));
+        it.off_up = op->Eup[c].off;
+        it.off_down = op->Edown[c].off;
+        ti.push_back(it);
+    }
+    TransferItem* d_ti = nullptr;
+    if ((rc = upload(ti, &d_ti, s))) { cleanup(); return rc; }
+    tmp.push_back(d_ti);
+    if (!ti.empty()) k_transfer<<<(unsigned)ti.size(), kb, 0, s>>>(d_ti, m, op->d_arena, tt);
+
+    // coupling
+    std::vector<CouplingItem> ci(op->far_t.size());
+    for (size_t b = 0; b < ci.size(); ++b) ci[b] = {op->far_t[b], op->far_s[b], op->S[b].off};
+    CouplingItem* d_ci = nullptr;
+    if ((rc = upload(ci, &d_ci, s))) { cleanup(); return rc; }
+    tmp.push_back(d_ci);
+    if (!ci.empty()) k_coupling<<<(unsigned)ci.size(), 256, 0, s>>>(d_ci, m, op->d_box, op->d_arena, tt);
+
     std::vector<NearItem> ni(op->near_t.size());
     int maxleaf = 1;
     for (size_t b = 0; b < ni.size(); ++b) {
@@ -517,9 +587,8 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
         maxleaf = std::max(maxleaf, std::max(it.t_size, it.s_size));
     }
     NearItem* d_ni = nullptr;
-    LeafTri* d_lt = nullptr;
-    if ((rc = upload(ni, &d_ni, s)) || (rc = upload(ltri, &d_lt, s))) { cleanup(); return rc; }
-    tmp.insert(tmp.end(), {d_ni, d_lt});
+    if ((rc = upload(ni, &d_ni, s))) { cleanup(); return rc; }
+    tmp.push_back(d_ni);
     if (!ni.empty()) {
         const size_t smem = sizeof(double) * (size_t)maxleaf * maxleaf;
         H2_CUDA_TRY(cudaFuncSetAttribute(k_near, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
