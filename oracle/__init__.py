@@ -248,6 +248,7 @@ class H2Oracle:
         return {"far_t": ft, "far_s": fs, "near_t": nt, "near_s": ns}
 
     def psi(self) -> np.ndarray:
+        """Psi at every node (``store=False``: only at nodes already sampled by ``rows``, NaN elsewhere)."""
         out = np.zeros(self.N)
         _lib().o2_get_psi(self._h, _pd(out))
         return out

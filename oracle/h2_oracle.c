@@ -137,17 +137,19 @@ void o_lindholm(const double* x, const double* r0, const double* r1, const doubl
 }
 
 /* Psi_i = sum over triangles not containing node i of Omega_T(xi_i). */
+static double psi_one(int64_t i, const double* xyz, int64_t T, const int32_t* tri) {
+    double s = 0.0;
+    for (int64_t t = 0; t < T; ++t) {
+        const int32_t* v = tri + 3 * t;
+        if (v[0] == i || v[1] == i || v[2] == i) continue;
+        s += o_solid_angle(xyz + 3 * i, xyz + 3 * v[0], xyz + 3 * v[1], xyz + 3 * v[2]);
+    }
+    return s;
+}
+
 void o_psi(int64_t N, const double* xyz, int64_t T, const int32_t* tri, double* psi) {
 #pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t i = 0; i < N; ++i) {
-        double s = 0.0;
-        for (int64_t t = 0; t < T; ++t) {
-            const int32_t* v = tri + 3 * t;
-            if (v[0] == i || v[1] == i || v[2] == i) continue;
-            s += o_solid_angle(xyz + 3 * i, xyz + 3 * v[0], xyz + 3 * v[1], xyz + 3 * v[2]);
-        }
-        psi[i] = s;
-    }
+    for (int64_t i = 0; i < N; ++i) psi[i] = psi_one(i, xyz, T, tri);
 }
 
 /* One full row of M: row[j] = M_ij for all j (row has N entries, zeroed here). */
@@ -564,7 +566,11 @@ void* o2_create(int64_t N, const double* xyz, int64_t T, const int32_t* tri, int
     o->m = m; o->k = m * m * m; o->leaf = leaf; o->eta = eta; o->rho = rho;
     o->q = q > 0 ? q : (3 * m - 1 + 1) / 2;   /* ceil((3m-1)/2) */
     o->psi = (double*)malloc(sizeof(double) * N);
-    o_psi(N, o->xyz, T, o->tri, o->psi);
+    if (store) {
+        o_psi(N, o->xyz, T, o->tri, o->psi);
+    } else {   /* sampled rows: Psi is evaluated for the sampled nodes only (o2_rows) */
+        for (int64_t i = 0; i < N; ++i) o->psi[i] = NAN;
+    }
     build_adjacency(o);
     build_tree(o);
     build_blocks(o);
@@ -766,6 +772,10 @@ void o2_rows(void* h, int32_t r, const double* x, int64_t nrows, const int64_t* 
         for (int c = leaf_of[pos[rows[q]]]; c >= 0; c = o->parent[c]) on_path[c] = 1;
     }
     for (int64_t b = 0; b < o->nfar; ++b) if (on_path[o->far_t[b]]) need[o->far_s[b]] = 1;
+    /* Psi at the sampled nodes (all nodes already have it when the near field is stored) */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < nrows; ++q)
+        if (isnan(o->psi[rows[q]])) o->psi[rows[q]] = psi_one(rows[q], o->xyz, o->T, o->tri);
     double** xh = (double**)calloc(o->nc, sizeof(double*));
 #pragma omp parallel for schedule(dynamic, 1)
     for (int c = 0; c < o->nc; ++c) {
