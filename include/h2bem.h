@@ -61,8 +61,8 @@ typedef enum {
  *             products with FP32 accumulation on the CUDA cores.
  *  H2_TF32X3: as H2_FP32, but the coupling and transfer products run on the
  *             tensor cores (tcgen05) as three TF32 products per term
- *             (hi*hi + hi*lo + lo*hi, hi = the value with its 13 low mantissa
- *             bits cleared, lo = the exact remainder), FP32 accumulation.
+ *             (hi*hi + hi*lo + lo*hi, hi = the nearest TF32 value, lo = the
+ *             nearest TF32 value of the remainder), FP32 accumulation.
  *  H2_BF16X3: coupling and transfer matrices stored as BF16 pairs hi + lo
  *             (hi = bf16(a), lo = bf16(a - hi), 4 bytes per entry) and
  *             multiplied on the tensor cores as hi*hi + hi*lo + lo*hi with the

@@ -135,6 +135,9 @@ struct KArgs {
     int tc;                    // the operator has tensor-core segments
     int tc_alo_bytes;          // shared memory for the TF32 lo parts of a chunk
     int tc_b_bytes;            // shared memory for each of the B hi / lo operands
+    int tc_sets;               // operand sets (2: the next chunk is prepared while the tensor core works)
+    int tc_cols;               // TMEM columns per CTA (power of 2, at most 512 / resident CTAs per SM)
+    int tc_nacc;               // accumulators of the hi*hi products (K steps round-robin)
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -309,9 +312,10 @@ __device__ __forceinline__ void write_segment(const StageDesc& D, const double* 
 //
 // A chunk of coupling or transfer blocks arrives as tensor tiles (see
 // tc_offset).  The consumer warps split the operands into hi and lo parts in
-// shared memory (TF32: hi = the FP32 value with its 13 low mantissa bits
-// cleared, written back in place, exactly representable in TF32; lo = the
-// exact remainder.  BF16: the tiles already hold hi and lo), build the
+// shared memory (TF32: hi = the nearest TF32 value, written back in place,
+// lo = the nearest TF32 value of the remainder, so that |a - hi - lo| and
+// |lo * lo| are below 2^-24 |a| and the tensor core's conversion is exact.
+// BF16: the tiles already hold hi and lo), build the
 // K-major B operand (the chunk's input vectors, N = r padded to the MMA's
 // granularity, hi and lo), and one thread issues, per K step, the three
 // products hi*hi + hi*lo + lo*hi into an FP32 accumulator in tensor memory
@@ -343,7 +347,13 @@ __device__ __forceinline__ void mma_issue(int type, uint32_t tmem, uint64_t a, u
                      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
                      : "memory");
 }
-__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+// Nearest TF32 value of an FP32 number (ties away from zero): adding half a
+// TF32 unit to the magnitude bits and clearing the 13 low mantissa bits.  The
+// result is exactly representable in TF32, so the tensor core's own conversion
+// leaves it unchanged.
+__device__ __forceinline__ float tf32_rn(float v) {
+    return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
+}
 // Byte offset of B entry (n, kk) in a K-major operand of Np rows (K slow).
 __device__ __forceinline__ int b_offset(int n, int kk, int Np, int es) {
     const int per = 16 / es;
@@ -392,19 +402,19 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
     // tensor-core operands: after the partial sums, or over them when there is
     // a single partial-sum buffer (its readers finish behind a consumer barrier
     // before the next chunk is prepared)
-    unsigned char* tc_alo = NRED == 1 ? reinterpret_cast<unsigned char*>(red)
-                                      : reinterpret_cast<unsigned char*>(red + NRED * kConsumers * RT);
-    unsigned char* tc_bhi = tc_alo + a.tc_alo_bytes;
-    unsigned char* tc_blo = tc_bhi + a.tc_b_bytes;
+    // operand set q: [lo parts of A][B hi][B lo] at tc_base + q * tc_set_bytes
+    unsigned char* tc_base = NRED == 1 ? reinterpret_cast<unsigned char*>(red)
+                                       : reinterpret_cast<unsigned char*>(red + NRED * kConsumers * RT);
+    const size_t tc_set_bytes = (size_t)a.tc_alo_bytes + 2 * (size_t)a.tc_b_bytes;
     const size_t red_span = (size_t)NRED * kConsumers * RT * sizeof(double);
-    const size_t tc_span = (size_t)a.tc_alo_bytes + 2 * (size_t)a.tc_b_bytes;
+    const size_t tc_span = (size_t)a.tc_sets * tc_set_bytes;
     uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(red) +
                                                   (NRED == 1 ? (red_span > tc_span ? red_span : tc_span)
                                                              : red_span + tc_span));
     uint64_t* empty = full + S;
     uint64_t* segbar = empty + S;
     uint64_t* cbar = segbar + 1;     // consumers: tensor operands ready
-    uint64_t* mmabar = cbar + 1;     // tensor-core products of a chunk done
+    uint64_t* mmabar = cbar + 1;     // [2]: tensor-core products of chunk n done (barrier n & 1)
     __shared__ StageDesc sd[kMaxStages];
     __shared__ SPiece spc[kMaxStages][H2_MAX_CHUNK_PIECES];
     __shared__ int abort_flag;
@@ -419,11 +429,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
         }
         mbar_init(segbar, kConsumers);
         mbar_init(cbar, kConsumers);
-        mbar_init(mmabar, 1);
+        mbar_init(&mmabar[0], 1);
+        mbar_init(&mmabar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (TC && tid < 32) {   // 32 TMEM columns: one FP32 accumulator of up to 128 rows x 32 RHS
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_addr(&tmem_base))
+    if (TC && tid < 32) {   // FP32 accumulators of up to 128 rows x Np right-hand sides
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(a.tc_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -562,8 +574,25 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
         double acc[RT];
 #pragma unroll
         for (int c = 0; c < RT; ++c) acc[c] = 0.0;
-        uint32_t segphase = 0, cphase = 0, mphase = 0;
-        bool tc_fresh = true;   // thread 0: the next product starts a segment's accumulator
+        uint32_t segphase = 0, cphase = 0;
+        int tcn = 0;            // tensor-core chunks so far
+        int segk = 0;           // K steps of the current tensor-core segment issued so far
+        int pend_st = -1;       // stage of the last tensor-core chunk, released once its products are done
+        int pend_n = 0;
+        // zero padding of B (right-hand sides r..Np-1) is written once when the
+        // operand sets do not share memory with the partial sums
+        const bool pad_once = NRED == 2;
+        if (TC && pad_once)
+            for (int q = tid; q < (int)(tc_span / 16); q += kConsumers)
+                reinterpret_cast<float4*>(tc_base)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        auto release_pending = [&]() -> bool {
+            if (!TC || pend_st < 0) return true;
+            if (!mbar_wait_or_abort(&mmabar[pend_n & 1], (uint32_t)(pend_n >> 1) & 1u, abortp)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            mbar_arrive(&empty[pend_st]);
+            pend_st = -1;
+            return true;
+        };
         for (int i = 0;; ++i) {
             const int st = i % S;
             if (!mbar_wait_or_abort(&full[st], (uint32_t)(i / S) & 1u, abortp)) {
@@ -582,22 +611,34 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                 const int Np = Mp == 64 ? (r + 7) / 8 * 8 : (r + 15) / 16 * 16;
                 const int ks = tc_kstep(type);
                 const int bes = type == PIECE_TF32 ? 4 : 2;
-                if (type == PIECE_TF32) {   // A = hi (in place) + lo
+                // one operand set: wait until the previous chunk's products are done
+                if (a.tc_sets == 1 && !release_pending()) {
+                    atomicExch(a.err, 1);
+                    abort_flag = 1;
+                    break;
+                }
+                unsigned char* set = tc_base + (size_t)(tcn % a.tc_sets) * tc_set_bytes;
+                unsigned char* t_alo = set;
+                unsigned char* t_bhi = set + a.tc_alo_bytes;
+                unsigned char* t_blo = t_bhi + a.tc_b_bytes;
+                if (type == PIECE_TF32) {   // A = hi (in place) + lo, both nearest TF32 values
                     float4* A4 = reinterpret_cast<float4*>(stg);
-                    float4* L4 = reinterpret_cast<float4*>(tc_alo);
+                    float4* L4 = reinterpret_cast<float4*>(t_alo);
                     for (int q = tid; q < D.cbytes / 16; q += kConsumers) {
                         const float4 v = A4[q];
-                        const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+                        const float4 h = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
                         A4[q] = h;
-                        L4[q] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+                        L4[q] = make_float4(tf32_rn(v.x - h.x), tf32_rn(v.y - h.y), tf32_rn(v.z - h.z),
+                                            tf32_rn(v.w - h.w));
                     }
                 }
                 // B operand: rows n < Np (right-hand sides), K = the pieces' input rows
                 // (each piece padded to whole K steps with zeros)
                 int ktot = 0;
                 for (int p = 0; p < D.npieces; ++p) ktot += (spc[st][p].ncols + ks - 1) / ks * ks;
-                for (int idx = tid; idx < ktot * Np; idx += kConsumers) {
-                    const int kk = idx / Np, n = idx - kk * Np;
+                const int nb = pad_once ? r : Np;   // columns written per chunk
+                for (int idx = tid; idx < ktot * nb; idx += kConsumers) {
+                    const int kk = idx / nb, n = idx - kk * nb;
                     int p = 0, kb = 0;
                     int kp0 = (spc[st][0].ncols + ks - 1) / ks * ks;
                     while (kk >= kb + kp0) {
@@ -612,13 +653,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                                         : 0.0f;
                     const int off = b_offset(n, kk, Np, bes);
                     if (type == PIECE_TF32) {
-                        const float h = tf32_hi(x);
-                        *reinterpret_cast<float*>(tc_bhi + off) = h;
-                        *reinterpret_cast<float*>(tc_blo + off) = x - h;
+                        const float h = tf32_rn(x);
+                        *reinterpret_cast<float*>(t_bhi + off) = h;
+                        *reinterpret_cast<float*>(t_blo + off) = tf32_rn(x - h);
                     } else {
                         const __nv_bfloat16 h = __float2bfloat16_rn(x);
-                        *reinterpret_cast<__nv_bfloat16*>(tc_bhi + off) = h;
-                        *reinterpret_cast<__nv_bfloat16*>(tc_blo + off) = __float2bfloat16_rn(x - __bfloat162float(h));
+                        *reinterpret_cast<__nv_bfloat16*>(t_bhi + off) = h;
+                        *reinterpret_cast<__nv_bfloat16*>(t_blo + off) = __float2bfloat16_rn(x - __bfloat162float(h));
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -628,75 +669,110 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                     abort_flag = 1;
                     break;
                 }
+                // K steps of this chunk (every consumer thread tracks the segment's count)
+                int csteps = 0;
+                for (int p = 0; p < D.npieces; ++p) csteps += (spc[st][p].ncols + ks - 1) / ks;
                 if (tid == 0) {
+                    // hi*hi of K step g goes to accumulator g % nacc, the two
+                    // correction products of every step to accumulator nacc: few
+                    // tensor-core accumulations per FP32 accumulator
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t idesc = mma_idesc(type, Mp, Np);
                     const uint32_t lboA = 16u * Mp, lboB = (uint32_t)(Np / 8) * 128u;
                     const int bper = 16 / bes;
-                    int kb = 0;
+                    const int nacc = a.tc_nacc;
+                    const uint32_t tcorr = tmem_base + (uint32_t)(nacc * Np);
+                    int kb = 0, gstep = segk;
                     for (int p = 0; p < D.npieces; ++p) {
                         const SPiece P = spc[st][p];
                         const int nst = (P.ncols + ks - 1) / ks;
-                        for (int q = 0; q < nst; ++q) {
+                        for (int q = 0; q < nst; ++q, ++gstep) {
                             const uint32_t aoff = (uint32_t)P.smem_off + (uint32_t)(q * ks * Mp * 4);
                             const uint32_t boff = (uint32_t)((kb + q * ks) / bper) * lboB;
                             const uint64_t ahi = smem_desc(smem_addr(stg) + aoff, lboA, 128);
                             const uint64_t alo = type == PIECE_TF32
-                                                     ? smem_desc(smem_addr(tc_alo) + aoff, lboA, 128)
+                                                     ? smem_desc(smem_addr(t_alo) + aoff, lboA, 128)
                                                      : smem_desc(smem_addr(stg) + aoff + 32u * Mp, lboA, 128);
-                            const uint64_t bhi = smem_desc(smem_addr(tc_bhi) + boff, lboB, 128);
-                            const uint64_t blo = smem_desc(smem_addr(tc_blo) + boff, lboB, 128);
-                            mma_issue(type, tmem_base, ahi, bhi, idesc, tc_fresh ? 0u : 1u);
-                            mma_issue(type, tmem_base, ahi, blo, idesc, 1u);
-                            mma_issue(type, tmem_base, alo, bhi, idesc, 1u);
-                            tc_fresh = false;
+                            const uint64_t bhi = smem_desc(smem_addr(t_bhi) + boff, lboB, 128);
+                            const uint64_t blo = smem_desc(smem_addr(t_blo) + boff, lboB, 128);
+                            const uint32_t tacc = tmem_base + (uint32_t)((gstep % nacc) * Np);
+                            mma_issue(type, tacc, ahi, bhi, idesc, gstep >= nacc ? 1u : 0u);
+                            mma_issue(type, tcorr, ahi, blo, idesc, gstep > 0 ? 1u : 0u);
+                            mma_issue(type, tcorr, alo, bhi, idesc, 1u);
                         }
                         kb += nst * ks;
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     smem_addr(mmabar))
+                                     smem_addr(&mmabar[tcn & 1]))
                                  : "memory");
-                    tc_fresh = D.last != 0;
                 }
-                if (!mbar_wait_or_abort(mmabar, mphase++ & 1u, abortp)) {
+                segk += csteps;
+                const int nused = segk < a.tc_nacc ? segk : a.tc_nacc;   // hi*hi accumulators written
+                // the previous chunk's products are done by now in the common case
+                if (!release_pending()) {
                     atomicExch(a.err, 1);
                     abort_flag = 1;
                     break;
                 }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                mbar_arrive(&empty[st]);
-                if (D.last && tid < 128) {   // the four lane-quarter warps read the accumulator
-                    const int w = tid >> 5, lane = tid & 31;
-                    const int row = Mp == 128 ? tid : (lane < 16 ? 16 * w + lane : -1);
-                    uint32_t v[32];
-                    const uint32_t taddr = tmem_base + ((uint32_t)(32 * w) << 16);
-#pragma unroll
-                    for (int c0 = 0; c0 < 32; c0 += 8) {
-                        if (c0 < Np)
-                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                         : "=r"(v[c0]), "=r"(v[c0 + 1]), "=r"(v[c0 + 2]), "=r"(v[c0 + 3]),
-                                           "=r"(v[c0 + 4]), "=r"(v[c0 + 5]), "=r"(v[c0 + 6]), "=r"(v[c0 + 7])
-                                         : "r"(taddr + (uint32_t)c0));
+                pend_st = st;
+                pend_n = tcn++;
+                if (D.last) {
+                    if (!release_pending()) {
+                        atomicExch(a.err, 1);
+                        abort_flag = 1;
+                        break;
                     }
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (row >= 0 && row < D.nrows) {
-                        float* dst = a.ws32 + (int64_t)(D.out_row + row) * r;
+                    if (tid < 128) {   // the four lane-quarter warps read and add the accumulators
+                        const int w = tid >> 5, lane = tid & 31;
+                        const int row = Mp == 128 ? tid : (lane < 16 ? 16 * w + lane : -1);
+                        float sum[32];
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) {
-                            if (c >= r) break;
-                            const float y = __uint_as_float(v[c]);
-                            if (D.mode == SEG_STORE) dst[c] = y;
-                            else if (D.mode == SEG_ADD) dst[c] = __ldcg(dst + c) + y;
-                            else atomicAdd(dst + c, y);
+                        for (int c = 0; c < 32; ++c) sum[c] = 0.0f;
+                        for (int j = 0; j <= nused; ++j) {   // nused hi*hi accumulators, then the corrections
+                            const int acc_col = (j < nused ? j : a.tc_nacc) * Np;
+                            uint32_t v[32];
+                            const uint32_t taddr = tmem_base + ((uint32_t)(32 * w) << 16) + (uint32_t)acc_col;
+#pragma unroll
+                            for (int c0 = 0; c0 < 32; c0 += 8) {
+                                if (c0 < Np)
+                                    asm volatile(
+                                        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                        : "=r"(v[c0]), "=r"(v[c0 + 1]), "=r"(v[c0 + 2]), "=r"(v[c0 + 3]),
+                                          "=r"(v[c0 + 4]), "=r"(v[c0 + 5]), "=r"(v[c0 + 6]), "=r"(v[c0 + 7])
+                                        : "r"(taddr + (uint32_t)c0));
+                            }
+                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                            for (int c = 0; c < 32; ++c)
+                                if (c < Np) sum[c] += __uint_as_float(v[c]);
+                        }
+                        if (row >= 0 && row < D.nrows) {
+                            float* dst = a.ws32 + (int64_t)(D.out_row + row) * r;
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) {
+                                if (c >= r) break;
+                                const float y = sum[c];
+                                if (D.mode == SEG_STORE) dst[c] = y;
+                                else if (D.mode == SEG_ADD) dst[c] = __ldcg(dst + c) + y;
+                                else atomicAdd(dst + c, y);
+                            }
+                        }
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        if (FLOW && D.signal >= 0) {
+                            __syncwarp();
+                            if (lane == 0) signal_region(a.cnt + D.signal);
                         }
                     }
-                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    if (FLOW && D.signal >= 0) {
-                        __syncwarp();
-                        if (lane == 0) signal_region(a.cnt + D.signal);
-                    }
+                    segk = 0;
                 }
                 continue;
+            }
+            // a CUDA-core chunk: the tensor core must be done with the operand
+            // sets (the partial sums may share their memory) and the stage
+            if (!release_pending()) {
+                atomicExch(a.err, 1);
+                abort_flag = 1;
+                break;
             }
             const int nrows = D.nrows;
             const int G = kConsumers / nrows;
@@ -735,6 +811,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                 }
             }
         }
+        // the tensor core finishes before its memory is released (bounded)
+        (void)release_pending();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -745,7 +823,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
     }
     if (TC && tid < 32) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem_base) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(a.tc_cols)
+                     : "memory");
     }
 }
 
@@ -823,9 +902,21 @@ cudaError_t launch_seg_rt(const KArgs& a, int nsm, size_t smem, cudaStream_t s, 
     static int occ = 0;
     cudaError_t e = set_smem(k_seg<RT, FLOW, TC>, smem, configured);
     if (e != cudaSuccess) return e;
-    const int g = std::max(1, std::min(a.nseg, nsm * ctas_per_sm(k_seg<RT, FLOW, TC>, smem, occ, occ_smem)));
+    const int per_sm = ctas_per_sm(k_seg<RT, FLOW, TC>, smem, occ, occ_smem);
+    const int g = std::max(1, std::min(a.nseg, nsm * per_sm));
     if (launched) *launched = g;
-    k_seg<RT, FLOW, TC><<<g, kBlock, smem, s>>>(a);
+    KArgs b = a;
+    if (TC) {
+        // TMEM columns per CTA: a power of 2 such that the resident CTAs of an SM
+        // never ask for more than its 512 columns (an allocation never waits);
+        // the hi*hi accumulators fill them after one for the corrections
+        int cols = 256;
+        while (cols * per_sm > 512 && cols > 32) cols >>= 1;
+        const int np = (a.r + 15) / 16 * 16;
+        b.tc_cols = cols;
+        b.tc_nacc = std::max(1, std::min(8, cols / np - 1));
+    }
+    k_seg<RT, FLOW, TC><<<g, kBlock, smem, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -880,6 +971,21 @@ static int tc_b_bytes(const h2_handle* op) {
     return op->stage_bytes / (4 * 64) * 32 * (p == H2_TF32X3 ? 4 : 2);
 }
 
+// Shared memory of the segment kernel with `sets` tensor-core operand sets.
+static size_t seg_smem_bytes(const h2_handle* op, int rt, int sets) {
+    const size_t S = (size_t)stages_for(rt);
+    const size_t red = (size_t)red_buffers(rt) * sizeof(double) * kConsumers * rt;
+    const size_t tc = (size_t)sets * ((size_t)tc_alo_bytes(op) + 2 * (size_t)tc_b_bytes(op));
+    const size_t mid = red_buffers(rt) == 1 ? std::max(red, tc) : red + tc;
+    return S * op->stage_bytes + S * xin_bytes(rt) + mid + sizeof(uint64_t) * (2 * S + 4);
+}
+
+// Two operand sets (chunk n+1 is prepared while the tensor core multiplies
+// chunk n) when they fit in a CTA's shared memory, else one.
+static int tc_sets_for(const h2_handle* op, int rt) {
+    return seg_smem_bytes(op, rt, 2) <= (size_t)220 * 1024 ? 2 : 1;
+}
+
 // Launches the gather kernel and every pass (level-wise) or the flow kernel
 // on workspaces `ws` (FP64) and `ws32` (FP32 operators only).
 int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream_t s, double* ws,
@@ -927,6 +1033,7 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
     a.tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
     a.tc_alo_bytes = tc_alo_bytes(op);
     a.tc_b_bytes = tc_b_bytes(op);
+    a.tc_sets = tc_sets_for(op, rt);
     if (flow) {
         a.seg = op->d_fseg;
         a.chunk = op->d_fchunk;
@@ -953,13 +1060,7 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
 
 }  // namespace
 
-size_t pass_smem_bytes(const h2_handle* op, int rt) {
-    const size_t S = (size_t)stages_for(rt);
-    const size_t red = (size_t)red_buffers(rt) * sizeof(double) * kConsumers * rt;
-    const size_t tc = (size_t)tc_alo_bytes(op) + 2 * (size_t)tc_b_bytes(op);
-    const size_t mid = red_buffers(rt) == 1 ? std::max(red, tc) : red + tc;
-    return S * op->stage_bytes + S * xin_bytes(rt) + mid + sizeof(uint64_t) * (2 * S + 3);
-}
+size_t pass_smem_bytes(const h2_handle* op, int rt) { return seg_smem_bytes(op, rt, tc_sets_for(op, rt)); }
 
 // Resident CTAs and per-CTA rates of the dataflow kernel on the current
 // device for the operator's largest r (input of the ticket-order simulation).

@@ -1,0 +1,64 @@
+"""GPU parity at the full sizes of the large synthetic workloads, on sampled rows.
+
+The CPU oracle computes selected rows of the H2 product exactly as its
+definition states (direct Chebyshev bases on every cluster's own box, exact
+Lindholm near entries, the solid-angle diagonal), one row at a time; the GPU
+computes the whole product in the launch configuration the benchmark times
+(dataflow schedule).  The rows are every node of two leaves (the first and a
+middle one of the tree), so that every level of the block tree contributes.
+
+Workloads (synth.workloads): the 1000 x 1000 x 10 film (209,922 nodes, m = 5),
+the 3:2:1 ellipsoid with 32 smooth right-hand sides (163,842 nodes, m = 5) and
+the level-8 icosphere with 16 right-hand sides (655,362 nodes, m = 5).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_1811_05731_gb300 as pkg  # noqa: E402
+import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-8
+TOL = {"fp64": FP64_TOL, "fp32": 1e-5, "tf32x3": 1e-5}
+# BF16 hi + lo stores about 17 significant bits (|a - hi - lo| <= 2^-17 |a|
+# with round-to-nearest hi and lo) against FP32's 24: its error is the FP32
+# form's error (the workload's amplification of per-entry rounding, measured
+# on the same rows) scaled by 2^(24 - 17), with a factor 2 of margin.
+BF16_OVER_FP32 = 2.0 * 2.0 ** (24 - 17)
+PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3}
+
+
+def sampled_rows(o):
+    tr = o.tree()
+    leaves = [c for c in range(len(tr["size"])) if tr["child0"][c] < 0]
+    pick = [leaves[0], leaves[len(leaves) // 2]]
+    return np.concatenate([tr["perm"][tr["start"][c]:tr["start"][c] + tr["size"][c]] for c in pick])
+
+
+@pytest.mark.parametrize("name", ["film", "ellipsoid", "ico8"])
+def test_full_size_sampled_rows(name):
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    w = synth.make_workload(name)
+    o = oracle.H2Oracle(w.mesh.xyz, w.mesh.tri, w.m, w.leaf, w.eta, store=False)
+    rows = sampled_rows(o)
+    ref = o.rows(w.u1, rows)                       # (r, nrows)
+    o.close()
+    g = pkg.Geometry(w.mesh.xyz, w.mesh.tri)
+    x = torch.from_numpy(np.ascontiguousarray(w.u1)).cuda()
+    errs = {}
+    for prec in ("fp64", "fp32", "tf32x3", "bf16x3"):
+        op = pkg.Operator(g, m=w.m, leaf=w.leaf, eta=w.eta, precision=PREC[prec], max_rhs=w.r)
+        y = op.matvec(x, torch.full_like(x, float("nan"))).cpu().numpy()[:, rows]
+        assert pkg.h2_device_status(op.handle) == 0
+        errs[prec] = float(np.max(np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+        del op
+        torch.cuda.empty_cache()
+    print(name, {k: f"{v:.2e}" for k, v in errs.items()})
+    for prec in ("fp64", "fp32", "tf32x3"):
+        assert errs[prec] <= TOL[prec], (prec, errs[prec])
+    assert errs["bf16x3"] <= BF16_OVER_FP32 * errs["fp32"], errs

@@ -115,10 +115,11 @@ def test_fp64_matvec_matches_oracle(name, mk, m_, leaf, r, schedule):
 PRECISIONS = {"fp32": 1, "tf32x3": 2, "bf16x3": 3}
 # Error budgets of the reduced forms against the FP64 oracle.  FP32 and 3xTF32
 # meet the 1e-5 target of the mixed forms.  BF16 hi + lo keeps about 17
-# significant bits (|a - hi - lo| <= 2^-18 |a|), and the far-field sums of this
-# operator amplify per-entry rounding about 7x (FP32: 2^-24 per entry, 4e-7
-# measured on the 64 x 64 cube), so its budget is 3e-5 (1.5e-5 measured there).
-REDUCED_TOL = {"fp32": MIXED_TOL, "tf32x3": MIXED_TOL, "bf16x3": 3e-5}
+# significant bits (|a - hi - lo| <= 2^-17 |a|), 2^7 times FP32's per-entry
+# rounding; on these meshes the far-field sums amplify per-entry rounding
+# about 7-30x (FP32 measured 1e-8 .. 5e-7), so its budget is 1e-4 (1.5e-5
+# measured on the 64 x 64 cube).
+REDUCED_TOL = {"fp32": MIXED_TOL, "tf32x3": MIXED_TOL, "bf16x3": 1e-4}
 
 
 @pytest.mark.parametrize("precision", sorted(PRECISIONS))
