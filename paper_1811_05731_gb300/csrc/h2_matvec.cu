@@ -633,33 +633,45 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                     }
                 }
                 // B operand: rows n < Np (right-hand sides), K = the pieces' input rows
-                // (each piece padded to whole K steps with zeros)
-                int ktot = 0;
-                for (int p = 0; p < D.npieces; ++p) ktot += (spc[st][p].ncols + ks - 1) / ks * ks;
-                const int nb = pad_once ? r : Np;   // columns written per chunk
-                for (int idx = tid; idx < ktot * nb; idx += kConsumers) {
-                    const int kk = idx / nb, n = idx - kk * nb;
-                    int p = 0, kb = 0;
-                    int kp0 = (spc[st][0].ncols + ks - 1) / ks * ks;
-                    while (kk >= kb + kp0) {
-                        kb += kp0;
-                        ++p;
-                        kp0 = (spc[st][p].ncols + ks - 1) / ks * ks;
-                    }
-                    const SPiece P = spc[st][p];
-                    const int j = kk - kb;
-                    const float x = (j < P.ncols && n < r)
-                                        ? reinterpret_cast<const float*>(xin + P.xoff)[j * r + n]
-                                        : 0.0f;
-                    const int off = b_offset(n, kk, Np, bes);
-                    if (type == PIECE_TF32) {
-                        const float h = tf32_rn(x);
-                        *reinterpret_cast<float*>(t_bhi + off) = h;
-                        *reinterpret_cast<float*>(t_blo + off) = tf32_rn(x - h);
-                    } else {
-                        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-                        *reinterpret_cast<__nv_bfloat16*>(t_bhi + off) = h;
-                        *reinterpret_cast<__nv_bfloat16*>(t_blo + off) = __float2bfloat16_rn(x - __bfloat162float(h));
+                // (each piece padded to whole K steps with zeros).  A work unit is one
+                // 16-byte core row: right-hand side n, `per` consecutive K rows (8 BF16
+                // or 4 TF32 values), written with one vector store per part.
+                {
+                    const int per = 16 / bes;
+                    const int nb = pad_once ? r : Np;   // right-hand sides written per chunk
+                    int kb = 0;
+                    for (int p = 0; p < D.npieces; ++p) {
+                        const SPiece P = spc[st][p];
+                        const int kp = (P.ncols + ks - 1) / ks * ks;
+                        const float* xp = reinterpret_cast<const float*>(xin + P.xoff);
+                        const int units = (kp / per) * nb;
+                        for (int u = tid; u < units; u += kConsumers) {
+                            const int kg = u / nb, n = u - kg * nb;   // K group, right-hand side
+                            const int j0 = kg * per;
+                            const int off = b_offset(n, kb + j0, Np, bes);
+                            if (type == PIECE_TF32) {
+                                float h[4], l[4];
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    const float x = (j0 + e < P.ncols && n < r) ? xp[(j0 + e) * r + n] : 0.0f;
+                                    h[e] = tf32_rn(x);
+                                    l[e] = tf32_rn(x - h[e]);
+                                }
+                                *reinterpret_cast<float4*>(t_bhi + off) = make_float4(h[0], h[1], h[2], h[3]);
+                                *reinterpret_cast<float4*>(t_blo + off) = make_float4(l[0], l[1], l[2], l[3]);
+                            } else {
+                                __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) {
+                                    const float x = (j0 + e < P.ncols && n < r) ? xp[(j0 + e) * r + n] : 0.0f;
+                                    h[e] = __float2bfloat16_rn(x);
+                                    l[e] = __float2bfloat16_rn(x - __bfloat162float(h[e]));
+                                }
+                                *reinterpret_cast<uint4*>(t_bhi + off) = *reinterpret_cast<const uint4*>(h);
+                                *reinterpret_cast<uint4*>(t_blo + off) = *reinterpret_cast<const uint4*>(l);
+                            }
+                        }
+                        kb += kp;
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -682,25 +694,29 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                     const int bper = 16 / bes;
                     const int nacc = a.tc_nacc;
                     const uint32_t tcorr = tmem_base + (uint32_t)(nacc * Np);
-                    int kb = 0, gstep = segk;
+                    // descriptors advance by adding (byte offset >> 4) to their
+                    // 14-bit start-address field (shared memory < 256 KB: no carry)
+                    const uint64_t dA0 = smem_desc(smem_addr(stg), lboA, 128);
+                    const uint64_t dL0 = type == PIECE_TF32 ? smem_desc(smem_addr(t_alo), lboA, 128)
+                                                            : dA0 + (uint64_t)((32u * Mp) >> 4);
+                    const uint64_t dBh = smem_desc(smem_addr(t_bhi), lboB, 128);
+                    const uint64_t dBl = smem_desc(smem_addr(t_blo), lboB, 128);
+                    const uint64_t a_step = (uint64_t)((ks * Mp * 4) >> 4);        // one K slab of A
+                    const uint64_t b_step = (uint64_t)(((ks / bper) * lboB) >> 4);  // one K step of B
+                    int gstep = segk;
+                    int accn = segk % nacc;
+                    uint64_t bo = 0;
                     for (int p = 0; p < D.npieces; ++p) {
                         const SPiece P = spc[st][p];
                         const int nst = (P.ncols + ks - 1) / ks;
-                        for (int q = 0; q < nst; ++q, ++gstep) {
-                            const uint32_t aoff = (uint32_t)P.smem_off + (uint32_t)(q * ks * Mp * 4);
-                            const uint32_t boff = (uint32_t)((kb + q * ks) / bper) * lboB;
-                            const uint64_t ahi = smem_desc(smem_addr(stg) + aoff, lboA, 128);
-                            const uint64_t alo = type == PIECE_TF32
-                                                     ? smem_desc(smem_addr(t_alo) + aoff, lboA, 128)
-                                                     : smem_desc(smem_addr(stg) + aoff + 32u * Mp, lboA, 128);
-                            const uint64_t bhi = smem_desc(smem_addr(t_bhi) + boff, lboB, 128);
-                            const uint64_t blo = smem_desc(smem_addr(t_blo) + boff, lboB, 128);
-                            const uint32_t tacc = tmem_base + (uint32_t)((gstep % nacc) * Np);
-                            mma_issue(type, tacc, ahi, bhi, idesc, gstep >= nacc ? 1u : 0u);
-                            mma_issue(type, tcorr, ahi, blo, idesc, gstep > 0 ? 1u : 0u);
-                            mma_issue(type, tcorr, alo, bhi, idesc, 1u);
+                        uint64_t ao = (uint64_t)(P.smem_off >> 4);
+                        for (int q = 0; q < nst; ++q, ++gstep, ao += a_step, bo += b_step) {
+                            const uint32_t tacc = tmem_base + (uint32_t)(accn * Np);
+                            mma_issue(type, tacc, dA0 + ao, dBh + bo, idesc, gstep >= nacc ? 1u : 0u);
+                            mma_issue(type, tcorr, dA0 + ao, dBl + bo, idesc, gstep > 0 ? 1u : 0u);
+                            mma_issue(type, tcorr, dL0 + ao, dBh + bo, idesc, 1u);
+                            if (++accn == nacc) accn = 0;
                         }
-                        kb += nst * ks;
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                      smem_addr(&mmabar[tcn & 1]))
@@ -725,36 +741,30 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                     if (tid < 128) {   // the four lane-quarter warps read and add the accumulators
                         const int w = tid >> 5, lane = tid & 31;
                         const int row = Mp == 128 ? tid : (lane < 16 ? 16 * w + lane : -1);
-                        float sum[32];
+                        const uint32_t tlane = tmem_base + ((uint32_t)(32 * w) << 16);
+                        float* dst = a.ws32 + (int64_t)(D.out_row + (row < 0 ? 0 : row)) * r;
+                        for (int c0 = 0; c0 < Np; c0 += 8) {   // 8 right-hand sides at a time
+                            float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                            for (int j = 0; j <= nused; ++j) {   // nused hi*hi accumulators, then the corrections
+                                const uint32_t col = (uint32_t)((j < nused ? j : a.tc_nacc) * Np + c0);
+                                uint32_t v[8];
+                                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]),
+                                               "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                                             : "r"(tlane + col));
+                                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) sum[c] = 0.0f;
-                        for (int j = 0; j <= nused; ++j) {   // nused hi*hi accumulators, then the corrections
-                            const int acc_col = (j < nused ? j : a.tc_nacc) * Np;
-                            uint32_t v[32];
-                            const uint32_t taddr = tmem_base + ((uint32_t)(32 * w) << 16) + (uint32_t)acc_col;
-#pragma unroll
-                            for (int c0 = 0; c0 < 32; c0 += 8) {
-                                if (c0 < Np)
-                                    asm volatile(
-                                        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                        : "=r"(v[c0]), "=r"(v[c0 + 1]), "=r"(v[c0 + 2]), "=r"(v[c0 + 3]),
-                                          "=r"(v[c0 + 4]), "=r"(v[c0 + 5]), "=r"(v[c0 + 6]), "=r"(v[c0 + 7])
-                                        : "r"(taddr + (uint32_t)c0));
+                                for (int c = 0; c < 8; ++c) sum[c] += __uint_as_float(v[c]);
                             }
-                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                            if (row >= 0 && row < D.nrows) {
 #pragma unroll
-                            for (int c = 0; c < 32; ++c)
-                                if (c < Np) sum[c] += __uint_as_float(v[c]);
-                        }
-                        if (row >= 0 && row < D.nrows) {
-                            float* dst = a.ws32 + (int64_t)(D.out_row + row) * r;
-#pragma unroll
-                            for (int c = 0; c < 32; ++c) {
-                                if (c >= r) break;
-                                const float y = sum[c];
-                                if (D.mode == SEG_STORE) dst[c] = y;
-                                else if (D.mode == SEG_ADD) dst[c] = __ldcg(dst + c) + y;
-                                else atomicAdd(dst + c, y);
+                                for (int c = 0; c < 8; ++c) {
+                                    if (c0 + c >= r) break;
+                                    float* d = dst + c0 + c;
+                                    if (D.mode == SEG_STORE) *d = sum[c];
+                                    else if (D.mode == SEG_ADD) *d = __ldcg(d) + sum[c];
+                                    else atomicAdd(d, sum[c]);
+                                }
                             }
                         }
                         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
