@@ -117,6 +117,22 @@ int h2_assemble(const h2_handle* geom, const h2_params* p, h2_handle** out_op);
  *   1 <= r <= max_rhs.  u1 and u2 must not overlap.  u2 is overwritten. */
 int h2_matvec(h2_handle* op, const double* u1, double* u2, int32_t r, void* cuda_stream);
 
+/* u2_i = M_i u1_i for several operators at once (several meshes, e.g. of
+ * uneven size): after one input gather per operator, ONE persistent kernel
+ * launch runs the products of all of them, their segments scheduled together
+ * (Eq. (denseMat) for each mesh).
+ *   ops:    n_ops distinct operator handles, 1 <= n_ops <= 16, on one device.
+ *   u1, u2: n_ops DEVICE pointers; u1[i], u2[i] are r[i] x N_i doubles,
+ *           row-major, mesh node order; they must not overlap.
+ *   r:      n_ops right-hand-side counts, 1 <= r[i] <= max_rhs of ops[i].
+ * Asynchronous on `cuda_stream`.  The first call for a set of operators
+ * builds and caches the combined schedule (host work and device arrays,
+ * released when one of the operators is freed).  A bounded device-side wait
+ * that gives up is reported by h2_device_status(ops[0]).  Calls involving
+ * the same operator must not overlap. */
+int h2_matvec_batched(h2_handle* const* ops, int32_t n_ops, const double* const* u1, double* const* u2,
+                      const int32_t* r, void* cuda_stream);
+
 /* u2 = M u1 like h2_matvec, for callers that cannot allocate device memory
  * while they apply the operator (for example a time-stepping loop that
  * reserved all device memory in advance, or an application whose device

@@ -81,13 +81,16 @@ def load(path: str | None = None):
         L.h2_assemble.argtypes = [_vp, ctypes.POINTER(Params), ctypes.POINTER(_vp)]
         L.h2_matvec.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
         L.h2_matvec_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
+        L.h2_matvec_batched.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_vp),
+                                        ctypes.POINTER(_vp), _c_i32, _vp]
         L.h2_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
         L.h2_get_tree.argtypes = [_vp] + [_c_i32] * 7 + [_c_d]
         L.h2_get_blocks.argtypes = [_vp] + [_c_i32] * 4
         L.h2_get_psi.argtypes = [_vp, _c_d]
         L.h2_device_status.argtypes = [_vp]
         L.h2_free.argtypes = [_vp]
-        for f in ("h2_build_geometry", "h2_assemble", "h2_matvec", "h2_matvec_noalloc", "h2_stats", "h2_get_tree",
+        for f in ("h2_build_geometry", "h2_assemble", "h2_matvec", "h2_matvec_noalloc", "h2_matvec_batched",
+                  "h2_stats", "h2_get_tree",
                   "h2_get_blocks", "h2_get_psi", "h2_device_status", "h2_free"):
             getattr(L, f).restype = ctypes.c_int
         _LIB = L
@@ -153,6 +156,25 @@ def h2_matvec_noalloc(op: int, u1_ptr: int, u2_ptr: int, r: int, stream=None) ->
     """u2 = M u1 on device pointers with the library's fixed scratch (no device allocation)."""
     _check(lib().h2_matvec_noalloc(op, u1_ptr, u2_ptr, int(r), _stream_ptr(stream)),
            "h2_matvec_noalloc")
+
+
+def h2_matvec_batched(ops, u1_ptrs, u2_ptrs, rs, stream=None) -> None:
+    """u2_i = M_i u1_i for several operators in one persistent launch (device pointers)."""
+    n = len(ops)
+    arr = lambda xs: (_vp * n)(*[_vp(int(x)) for x in xs])
+    rr = (ctypes.c_int32 * n)(*[int(x) for x in rs])
+    _check(lib().h2_matvec_batched(arr(ops), n, arr(u1_ptrs), arr(u2_ptrs), rr, _stream_ptr(stream)),
+           "h2_matvec_batched")
+
+
+def matvec_batched(operators, xs, ys=None, stream=None):
+    """Batched product of ``Operator`` objects on torch CUDA tensors ``xs`` (each (r_i, N_i))."""
+    import torch
+    xs = [x if x.dim() == 2 else x.unsqueeze(0) for x in xs]
+    ys = ys if ys is not None else [torch.empty_like(x) for x in xs]
+    h2_matvec_batched([o.handle for o in operators], [x.data_ptr() for x in xs], [y.data_ptr() for y in ys],
+                      [x.shape[0] for x in xs], stream)
+    return ys
 
 
 def h2_stats(op: int) -> dict:

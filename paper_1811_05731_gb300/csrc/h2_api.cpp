@@ -1,6 +1,7 @@
 // C ABI of the h2bem library (declared in include/h2bem.h).  Argument checks,
 // handle life cycle and host <-> device staging; the numeric work is in
 // h2_assemble.cu and h2_matvec.cu.
+#include <atomic>
 #include <chrono>
 #include <cstring>
 #include <new>
@@ -130,6 +131,8 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
     h2_handle* geom = const_cast<h2_handle*>(geom_c);
     h2_handle* op = new (std::nothrow) h2_handle();
     if (!op) return H2_ERR_OOM;
+    static std::atomic<uint64_t> next_serial{1};
+    op->serial = next_serial++;
     op->kind = 2;
     op->geom = geom;
     geom->refcount++;
@@ -314,8 +317,27 @@ int h2_get_psi(const h2_handle* h, double* psi) {
 int h2_free(h2_handle* h) {
     if (!h) return H2_OK;
     if (h->kind != 1 && h->kind != 2) return H2_ERR_WRONG_HANDLE;
+    if (h->kind == 2) h2::drop_batch_plans(h->serial);
     release(h);
     return H2_OK;
+}
+
+int h2_matvec_batched(h2_handle* const* ops, int32_t n_ops, const double* const* u1, double* const* u2,
+                      const int32_t* r, void* cuda_stream) {
+    if (!ops || !u1 || !u2 || !r || n_ops < 1 || n_ops > H2_MAX_BATCH) return H2_ERR_INVALID_ARG;
+    for (int i = 0; i < n_ops; ++i) {
+        if (!ops[i] || !u1[i] || !u2[i]) return H2_ERR_INVALID_ARG;
+        if (ops[i]->kind != 2) return H2_ERR_WRONG_HANDLE;
+        if (r[i] < 1) return H2_ERR_INVALID_ARG;
+        if (r[i] > ops[i]->params.max_rhs) return H2_ERR_RHS_EXCEEDS_MAX;
+        if (!is_device_pointer(u1[i]) || !is_device_pointer(u2[i])) return H2_ERR_INVALID_ARG;
+        const size_t bytes = sizeof(double) * (size_t)ops[i]->geom->N * r[i];
+        const char *a = (const char*)u1[i], *b = (const char*)u2[i];
+        if (a < b + bytes && b < a + bytes) return H2_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (ops[j] == ops[i]) return H2_ERR_INVALID_ARG;   // one workspace per operator
+    }
+    return h2::matvec_batched(ops, n_ops, u1, u2, r, (cudaStream_t)cuda_stream);
 }
 
 }  // extern "C"

@@ -24,6 +24,7 @@
 #define H2_MAX_K 125
 #define H2_MAX_LEAF 128
 #define H2_MAX_RHS 32
+#define H2_MAX_BATCH 16        // operators of one batched product
 #define H2_MAX_CHUNK_COLS 128   // input columns of one chunk (shared-memory staging)
 #define H2_MAX_CHUNK_PIECES 32  // matrices of one chunk (one producer lane each)
 
@@ -134,6 +135,22 @@ struct FlowSeg {
     int32_t signal;      // region completed by this segment (-1: none)
     int32_t dep0, ndep;
     int32_t kind;        // PassKind of the originating pass
+    int32_t op;          // operator of a batched launch (0 for one operator)
+    int32_t pad;
+};
+
+// The dataflow form of one or several operators (one launch): segments in
+// ticket order, their chunks and pieces, the regions each segment waits for,
+// the number of signals that completes every region, and per operator the
+// y-hat rows cleared before the launch.  Regions of operator i are numbered
+// after those of operators 0..i-1 (3 n_clusters each).
+struct FlowOut {
+    std::vector<FlowSeg> seg;
+    std::vector<Chunk> chunk;
+    std::vector<Piece> piece;
+    std::vector<int32_t> deps, expect;
+    std::vector<std::vector<int32_t>> zero_rows;
+    int nreg = 0;
 };
 
 // Where one matrix lives in the arena.
@@ -147,6 +164,7 @@ struct MatRef {
 struct h2_handle {
     int kind = 0;   // 1 geometry, 2 operator
     int refcount = 1;
+    uint64_t serial = 0;   // unique per handle (keys the batched-launch plans)
 
     // ---------------- geometry ----------------
     int64_t N = 0, T = 0;
@@ -254,6 +272,7 @@ void build_block_partition(h2_handle* op);
 void gauss_legendre_unit(int q, std::vector<double>& x, std::vector<double>& w);
 void build_plan(h2_handle* op);   // arena layout + passes (h2_plan.cpp)
 double build_flow(h2_handle* op, const FlowModel& fm);   // dataflow order (h2_plan.cpp)
+double build_flow_multi(const std::vector<h2_handle*>& ops, const FlowModel& fm, FlowOut& out);
 
 // device-side assembly and matvec (h2_assemble.cu, h2_matvec.cu)
 int geometry_device_setup(h2_handle* g, cudaStream_t s);
@@ -265,6 +284,10 @@ void release_profile(h2_handle* op);
 int read_profile(h2_handle* op, std::vector<double>& ms, int& ncalls);
 size_t pass_smem_bytes(const h2_handle* op, int rt);
 int flow_model(h2_handle* op, FlowModel& fm);   // CTAs and rates of the device
+// One persistent launch over several operators (h2_matvec_batched).
+int matvec_batched(h2_handle* const* ops, int n, const double* const* u1, double* const* u2, const int32_t* r,
+                   cudaStream_t s);
+void drop_batch_plans(uint64_t serial);   // forget the plans that use an operator
 }  // namespace h2
 
 #define H2_CUDA_TRY(call)                                        \

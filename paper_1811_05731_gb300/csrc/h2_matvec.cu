@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -103,6 +104,8 @@ struct StageDesc {
     int32_t out_f32;   // 1 if the segment's output rows are FP32
     int32_t ptype;     // PieceType of the chunk's matrices
     int32_t cbytes;    // bytes of the chunk's matrices in the stage
+    int32_t op;        // operator (batched launches)
+    int32_t pad;
 };
 
 // One matrix of a staged chunk, as the consumers read it.
@@ -113,6 +116,18 @@ struct SPiece {
     int32_t xoff;       // byte offset of its input inside the stage's input buffer
 };
 
+// What a segment of operator `op` needs of its operator.
+struct OpCtx {
+    const unsigned char* arena;
+    double* ws;                // FP64 workspace
+    float* ws32;               // FP32 workspace (reduced-precision operators)
+    double* u2;
+    const int32_t* perm;
+    int64_t N;
+    int r;
+    int pad;
+};
+
 struct KArgs {
     const FlowSeg* seg;        // segments (dataflow form: in ticket order)
     const Chunk* chunk;
@@ -120,16 +135,10 @@ struct KArgs {
     const int32_t* deps;       // dataflow form only
     const int32_t* expect;     // dataflow form only
     int32_t* cnt;              // dataflow form: region counters, ticket counter at [nreg]
-    const unsigned char* arena;
-    double* ws;                // FP64 workspace
-    float* ws32;               // FP32 workspace (FP32 operators)
-    double* u2;
-    const int32_t* perm;
     int* err;
-    int64_t N;
     int nseg;
     int nreg;
-    int r;
+    int r;                     // largest r of the launch's operators
     int stages;
     int stage_bytes;
     int tc;                    // the operator has tensor-core segments
@@ -138,6 +147,8 @@ struct KArgs {
     int tc_sets;               // operand sets (2: the next chunk is prepared while the tensor core works)
     int tc_cols;               // TMEM columns per CTA (power of 2, at most 512 / resident CTAs per SM)
     int tc_nacc;               // accumulators of the hi*hi products (K steps round-robin)
+    int nops;                  // operators of the launch (several: a batched product)
+    OpCtx ctx[H2_MAX_BATCH];
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -195,13 +206,13 @@ __device__ __forceinline__ int input_bytes(int ncols, int r, bool f32) {
 // complete on the stage's `full` barrier.  Workspace values written by other
 // CTAs of the launch were published with release/acquire on the region
 // counters; the proxy fence orders them before these async-proxy reads.
-__device__ __forceinline__ void issue_inputs(const KArgs& a, const SPiece* pc, int npieces, bool f32,
+__device__ __forceinline__ void issue_inputs(const OpCtx& c, const SPiece* pc, int npieces, bool f32,
                                              unsigned char* xin, uint64_t* bar, int lane) {
     if (lane < npieces) {
         const SPiece P = pc[lane];
-        const int bytes = input_bytes(P.ncols, a.r, f32);
-        const unsigned char* src = f32 ? reinterpret_cast<const unsigned char*>(a.ws32 + (int64_t)P.in_row * a.r)
-                                       : reinterpret_cast<const unsigned char*>(a.ws + (int64_t)P.in_row * a.r);
+        const int bytes = input_bytes(P.ncols, c.r, f32);
+        const unsigned char* src = f32 ? reinterpret_cast<const unsigned char*>(c.ws32 + (int64_t)P.in_row * c.r)
+                                       : reinterpret_cast<const unsigned char*>(c.ws + (int64_t)P.in_row * c.r);
         asm volatile("fence.proxy.async.global;" ::: "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -501,7 +512,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
             const bool f32 = ctype != PIECE_F64;   // FP32 inputs (FP32 workspace)
             if (lane == 0) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                tma_load(stage_base + (size_t)st * a.stage_bytes, a.arena + csrc, (uint32_t)cbytes, &full[st]);
+                tma_load(stage_base + (size_t)st * a.stage_bytes, a.ctx[F.op].arena + csrc, (uint32_t)cbytes, &full[st]);
             }
             ++issued;
             const bool last = ci == F.s.nchunks - 1;
@@ -517,12 +528,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
             // offsets of the pieces' inputs in the stage's input buffer
             int in_total;
             if (cnp == 1) {
-                in_total = input_bytes(cncols, a.r, f32);
+                in_total = input_bytes(cncols, a.ctx[F.op].r, f32);
                 if (lane == 0) spc[st][0] = SPiece{0, cin0, cncols, 0};
             } else {
                 Piece pc{};
                 if (lane < cnp) pc = a.piece[cpiece0 + lane];
-                const int mine = lane < cnp ? input_bytes(pc.ncols, a.r, f32) : 0;
+                const int mine = lane < cnp ? input_bytes(pc.ncols, a.ctx[F.op].r, f32) : 0;
                 int xoff = mine;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -549,7 +560,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                              "r"(in_total)
                              : "memory");
             __syncwarp();
-            issue_inputs(a, spc[st], cnp, f32, xbase + (size_t)st * kXin, &full[st], lane);
+            issue_inputs(a.ctx[F.op], spc[st], cnp, f32, xbase + (size_t)st * kXin, &full[st], lane);
             if (lane == 0) {
                 StageDesc D;
                 D.seg = sg;
@@ -562,6 +573,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                 D.out_f32 = F.s.out_f32;
                 D.ptype = ctype;
                 D.cbytes = cbytes;
+                D.op = F.op;
                 D.signal = F.signal;
                 sd[st] = D;
                 mbar_arrive(&full[st]);
@@ -570,7 +582,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
         }
     } else {
         // ---------------- consumer warps ----------------
-        const int r = a.r;
         double acc[RT];
 #pragma unroll
         for (int c = 0; c < RT; ++c) acc[c] = 0.0;
@@ -602,6 +613,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
             }
             const StageDesc D = sd[st];
             if (D.seg < 0) break;
+            const OpCtx& C = a.ctx[D.op];
+            const int r = C.r;
             if (TC && piece_tc(D.ptype)) {
                 // ---------- tensor-core chunk ----------
                 unsigned char* stg = stage_base + (size_t)st * a.stage_bytes;
@@ -742,7 +755,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                         const int w = tid >> 5, lane = tid & 31;
                         const int row = Mp == 128 ? tid : (lane < 16 ? 16 * w + lane : -1);
                         const uint32_t tlane = tmem_base + ((uint32_t)(32 * w) << 16);
-                        float* dst = a.ws32 + (int64_t)(D.out_row + (row < 0 ? 0 : row)) * r;
+                        float* dst = C.ws32 + (int64_t)(D.out_row + (row < 0 ? 0 : row)) * r;
                         for (int c0 = 0; c0 < Np; c0 += 8) {   // 8 right-hand sides at a time
                             float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                             for (int j = 0; j <= nused; ++j) {   // nused hi*hi accumulators, then the corrections
@@ -806,7 +819,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                     break;
                 }
                 const bool writer = (tid >> 5) < writer_warps(nrows);
-                if (writer) write_segment<RT>(D, rb, r, G, a.ws, a.ws32, a.u2, a.perm, a.N);
+                if (writer) write_segment<RT>(D, rb, r, G, C.ws, C.ws32, C.u2, C.perm, C.N);
                 if (NRED == 1) {   // the single buffer is rewritten by the next segment
                     mbar_arrive(segbar);
                     if (!mbar_wait_or_abort(segbar, segphase++ & 1u, abortp)) {
@@ -981,19 +994,26 @@ static int tc_b_bytes(const h2_handle* op) {
     return op->stage_bytes / (4 * 64) * 32 * (p == H2_TF32X3 ? 4 : 2);
 }
 
-// Shared memory of the segment kernel with `sets` tensor-core operand sets.
-static size_t seg_smem_bytes(const h2_handle* op, int rt, int sets) {
+// Shared memory of the segment kernel with `sets` tensor-core operand sets of
+// `alo` + 2 `b` bytes.
+static size_t seg_smem_raw(int rt, int stage_bytes, int alo, int b, int sets) {
     const size_t S = (size_t)stages_for(rt);
     const size_t red = (size_t)red_buffers(rt) * sizeof(double) * kConsumers * rt;
-    const size_t tc = (size_t)sets * ((size_t)tc_alo_bytes(op) + 2 * (size_t)tc_b_bytes(op));
+    const size_t tc = (size_t)sets * ((size_t)alo + 2 * (size_t)b);
     const size_t mid = red_buffers(rt) == 1 ? std::max(red, tc) : red + tc;
-    return S * op->stage_bytes + S * xin_bytes(rt) + mid + sizeof(uint64_t) * (2 * S + 4);
+    return S * (size_t)stage_bytes + S * xin_bytes(rt) + mid + sizeof(uint64_t) * (2 * S + 4);
 }
 
 // Two operand sets (chunk n+1 is prepared while the tensor core multiplies
 // chunk n) when they fit in a CTA's shared memory, else one.
+static int tc_sets_raw(int rt, int stage_bytes, int alo, int b) {
+    return seg_smem_raw(rt, stage_bytes, alo, b, 2) <= (size_t)220 * 1024 ? 2 : 1;
+}
+static size_t seg_smem_bytes(const h2_handle* op, int rt, int sets) {
+    return seg_smem_raw(rt, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op), sets);
+}
 static int tc_sets_for(const h2_handle* op, int rt) {
-    return seg_smem_bytes(op, rt, 2) <= (size_t)220 * 1024 ? 2 : 1;
+    return tc_sets_raw(rt, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op));
 }
 
 // Launches the gather kernel and every pass (level-wise) or the flow kernel
@@ -1030,13 +1050,9 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
     }
     H2_CUDA_TRY(mark());
     KArgs a{};
-    a.arena = op->d_arena;
-    a.ws = ws;
-    a.ws32 = ws32;
-    a.u2 = u2;
-    a.perm = op->d_perm;
+    a.nops = 1;
+    a.ctx[0] = OpCtx{op->d_arena, ws, ws32, u2, op->d_perm, N, r, 0};
     a.err = op->d_err;
-    a.N = N;
     a.r = r;
     a.stages = stages_for(rt);
     a.stage_bytes = op->stage_bytes;
@@ -1074,14 +1090,11 @@ size_t pass_smem_bytes(const h2_handle* op, int rt) { return seg_smem_bytes(op, 
 
 // Resident CTAs and per-CTA rates of the dataflow kernel on the current
 // device for the operator's largest r (input of the ticket-order simulation).
-int flow_model(h2_handle* op, FlowModel& fm) {
+static int flow_model_raw(int rt, bool tc, size_t smem, int r, FlowModel& fm) {
     int dev = 0, nsm = 0, khz = 0;
     H2_CUDA_TRY(cudaGetDevice(&dev));
     H2_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     H2_CUDA_TRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
-    const int rt = rt_for(op->params.max_rhs);
-    const size_t smem = pass_smem_bytes(op, rt);
-    const bool tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
     int occ = 1;
     switch (rt) {
         case 1: occ = tc ? seg_occupancy<1, true>(smem) : seg_occupancy<1, false>(smem); break;
@@ -1093,11 +1106,17 @@ int flow_model(h2_handle* op, FlowModel& fm) {
     }
     const double ghz = khz > 0 ? khz * 1e-6 : 2.07;
     fm.workers = nsm * occ;
-    fm.r = op->params.max_rhs;
+    fm.r = r;
     fm.f64_per_ns = 2.0 * ghz / occ;
     fm.f32_per_ns = 128.0 * ghz / occ;
     fm.bytes_per_ns = 6800.0 / fm.workers;
     return H2_OK;
+}
+
+int flow_model(h2_handle* op, FlowModel& fm) {
+    const int rt = rt_for(op->params.max_rhs);
+    const bool tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
+    return flow_model_raw(rt, tc, pass_smem_bytes(op, rt), op->params.max_rhs, fm);
 }
 
 // Checks, on the host, the invariants the bulk copies rely on (16-byte aligned
@@ -1146,7 +1165,7 @@ int upload_plan(h2_handle* op) {
     int rc;
     for (Pass& p : op->passes) {
         std::vector<FlowSeg> fs(p.seg.size());
-        for (size_t i = 0; i < p.seg.size(); ++i) fs[i] = FlowSeg{p.seg[i], -1, 0, 0, p.kind};
+        for (size_t i = 0; i < p.seg.size(); ++i) fs[i] = FlowSeg{p.seg[i], -1, 0, 0, p.kind, 0, 0};
         if ((rc = upload_vec(fs, &p.d_seg)) || (rc = upload_vec(p.chunk, &p.d_chunk)) ||
             (rc = upload_vec(p.piece, &p.d_piece)))
             return rc;
@@ -1211,6 +1230,130 @@ int matvec_device(h2_handle* op, const double* u1, double* u2, int r, cudaStream
                            op->prof_enabled ? &ev : nullptr, &op->prof_pool);
     if (op->prof_enabled) op->prof_calls.push_back(std::move(ev));
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Batched product over several operators: their dataflow segments merged into
+// one ticket order (list-scheduled together), one input gather per operator,
+// then ONE persistent launch; every segment finds its operator's arena,
+// workspaces, u2, permutation, N and r in a context table passed with the
+// launch.  Merged schedules are cached per set of operators.
+// ---------------------------------------------------------------------------
+namespace {
+struct BatchPlan {
+    std::vector<uint64_t> serials;
+    FlowOut fo;
+    FlowSeg* d_seg = nullptr;
+    Chunk* d_chunk = nullptr;
+    Piece* d_piece = nullptr;
+    int32_t* d_deps = nullptr;
+    int32_t* d_expect = nullptr;
+    int32_t* d_cnt = nullptr;
+    std::vector<int32_t*> d_zero;
+    int grid = 0;
+    ~BatchPlan() {
+        for (void* p : {(void*)d_seg, (void*)d_chunk, (void*)d_piece, (void*)d_deps, (void*)d_expect, (void*)d_cnt})
+            if (p) cudaFree(p);
+        for (int32_t* p : d_zero)
+            if (p) cudaFree(p);
+    }
+};
+std::mutex g_batch_mu;
+std::vector<std::unique_ptr<BatchPlan>> g_batches;
+}  // namespace
+
+void drop_batch_plans(uint64_t serial) {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    g_batches.erase(std::remove_if(g_batches.begin(), g_batches.end(),
+                                   [&](const std::unique_ptr<BatchPlan>& b) {
+                                       return std::find(b->serials.begin(), b->serials.end(), serial) !=
+                                              b->serials.end();
+                                   }),
+                    g_batches.end());
+}
+
+int matvec_batched(h2_handle* const* ops, int n, const double* const* u1, double* const* u2, const int32_t* r,
+                   cudaStream_t s) {
+    int rmax = 1, alo = 0, b = 0;
+    bool tc = false;
+    for (int i = 0; i < n; ++i) {
+        rmax = std::max(rmax, (int)r[i]);
+        alo = std::max(alo, tc_alo_bytes(ops[i]));
+        b = std::max(b, tc_b_bytes(ops[i]));
+        tc = tc || ops[i]->params.precision == H2_TF32X3 || ops[i]->params.precision == H2_BF16X3;
+        if (ops[i]->stage_bytes != ops[0]->stage_bytes || ops[i]->device != ops[0]->device) return H2_ERR_INVALID_ARG;
+    }
+    const int rt = rt_for(rmax);
+    const int stage_bytes = ops[0]->stage_bytes;
+    const int sets = tc ? tc_sets_raw(rt, stage_bytes, alo, b) : 1;
+    const size_t smem = seg_smem_raw(rt, stage_bytes, alo, b, sets);
+    std::vector<uint64_t> key(n);
+    for (int i = 0; i < n; ++i) key[i] = ops[i]->serial;
+    BatchPlan* bp = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        for (auto& p : g_batches)
+            if (p->serials == key) bp = p.get();
+    }
+    if (!bp) {
+        auto nb = std::make_unique<BatchPlan>();
+        nb->serials = key;
+        FlowModel fm;
+        int rc = flow_model_raw(rt, tc, smem, rmax, fm);
+        if (rc != H2_OK) return rc;
+        if (build_flow_multi(std::vector<h2_handle*>(ops, ops + n), fm, nb->fo) < 0.0) {
+            set_last_error("h2_matvec_batched: no dataflow order exists for these operators");
+            return H2_ERR_INVALID_ARG;
+        }
+        // (the chunks are copies of the operators' own chunks, checked when each
+        // operator was assembled)
+        if ((rc = upload_vec(nb->fo.seg, &nb->d_seg)) || (rc = upload_vec(nb->fo.chunk, &nb->d_chunk)) ||
+            (rc = upload_vec(nb->fo.piece, &nb->d_piece)) || (rc = upload_vec(nb->fo.deps, &nb->d_deps)) ||
+            (rc = upload_vec(nb->fo.expect, &nb->d_expect)))
+            return rc;
+        H2_CUDA_TRY(cudaMalloc((void**)&nb->d_cnt, sizeof(int32_t) * ((size_t)nb->fo.nreg + 1)));
+        nb->d_zero.assign(n, nullptr);
+        for (int i = 0; i < n; ++i)
+            if ((rc = upload_vec(nb->fo.zero_rows[i], &nb->d_zero[i]))) return rc;
+        bp = nb.get();
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        g_batches.push_back(std::move(nb));
+    }
+    // gather every operator's input; the first gather also clears the counters
+    for (int i = 0; i < n; ++i) {
+        h2_handle* op = ops[i];
+        const std::vector<int32_t>& zr = bp->fo.zero_rows[i];
+        const int nclear = i == 0 ? bp->fo.nreg + 1 : 0;
+        const int64_t work =
+            std::max<int64_t>({op->row_xhat * r[i], (int64_t)zr.size() * op->kp * r[i], (int64_t)nclear});
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 4096));
+        k_prologue<<<grid, 256, 0, s>>>(u1[i], op->d_ws, op->d_ws32, op->d_gather_src, op->row_xhat, op->geom->N,
+                                        r[i], bp->d_zero[i], (int)zr.size(), op->kp, bp->d_cnt, nclear);
+        H2_CUDA_TRY(cudaGetLastError());
+    }
+    KArgs a{};
+    a.nops = n;
+    for (int i = 0; i < n; ++i)
+        a.ctx[i] = OpCtx{ops[i]->d_arena, ops[i]->d_ws, ops[i]->d_ws32, u2[i], ops[i]->d_perm, ops[i]->geom->N,
+                         (int)r[i], 0};
+    a.err = ops[0]->d_err;
+    a.r = rmax;
+    a.stages = stages_for(rt);
+    a.stage_bytes = stage_bytes;
+    a.tc = tc;
+    a.tc_alo_bytes = alo;
+    a.tc_b_bytes = b;
+    a.tc_sets = sets;
+    a.seg = bp->d_seg;
+    a.chunk = bp->d_chunk;
+    a.piece = bp->d_piece;
+    a.deps = bp->d_deps;
+    a.expect = bp->d_expect;
+    a.cnt = bp->d_cnt;
+    a.nseg = (int)bp->fo.seg.size();
+    a.nreg = bp->fo.nreg;
+    H2_CUDA_TRY(launch_seg<true>(a, rt, ops[0]->nsm, smem, s, &bp->grid));
+    return H2_OK;
 }
 
 }  // namespace h2

@@ -345,92 +345,96 @@ void build_plan(h2_handle* op) {
 // multiply-adds and matrix bytes at one CTA's share of the SM and HBM rates.
 // Returns the simulated makespan in microseconds (or -1 if the dataflow form
 // could not be built; the level-wise launches are used then).
-double build_flow(h2_handle* op, const FlowModel& fm) {
-    const int nc = op->nc;
-    const int kp = op->kp;
-    const int64_t N = op->geom->N;
-    op->fseg.clear();
-    op->fchunk.clear();
-    op->fpiece.clear();
-    op->fdeps.clear();
-    op->fexpect.assign((size_t)3 * nc, 0);
-    op->fzero_rows.clear();
-    op->use_flow = 0;
-
-    auto cluster_of_row = [&](int64_t row, int& region_base) -> int {
-        if (row < op->row_xhat) { region_base = -1; return -1; }
-        if (row < op->row_yhat) { region_base = 0; return (int)((row - op->row_xhat) / kp); }
-        region_base = nc;
-        return (int)((row - op->row_yhat) / kp);
-    };
-    std::vector<int32_t> leaf_at(N + 1, -1);
-    for (int c = 0; c < nc; ++c)
-        if (op->child0[c] < 0) leaf_at[op->start[c]] = c;
-
+double build_flow_multi(const std::vector<h2_handle*>& ops, const FlowModel& fm, FlowOut& out) {
+    out = FlowOut{};
     struct Item {
         FlowSeg fs;
         std::vector<int32_t> deps;
         double cost = 0.0, blevel = 0.0;
     };
     std::vector<Item> items;
-    std::vector<char> zero(nc, 0);
     const double r = std::max(1, fm.r);
-    for (const Pass& p : op->passes) {
-        for (const Segment& sg0 : p.seg) {
-            Item it{};
-            it.fs.s = sg0;
-            it.fs.kind = p.kind;
-            it.fs.s.chunk0 = (int32_t)op->fchunk.size();
-            double mac64 = 0.0, mac32 = 0.0, bytes = 0.0;
-            for (int q = 0; q < sg0.nchunks; ++q) {
-                Chunk ch = p.chunk[(size_t)sg0.chunk0 + q];
-                const int32_t pbase = (int32_t)op->fpiece.size();
-                bytes += ch.bytes;
-                for (int u = 0; u < ch.npieces; ++u) {
-                    const Piece pc = p.piece[(size_t)ch.piece0 + u];
-                    op->fpiece.push_back(pc);
-                    (pc.type == PIECE_F64 ? mac64 : mac32) += (double)sg0.nrows * pc.ncols * r;
+    int reg_base = 0;
+    std::vector<int32_t> producers;   // per region
+    out.zero_rows.resize(ops.size());
+    for (size_t oi = 0; oi < ops.size(); ++oi) {
+        h2_handle* op = ops[oi];
+        const int nc = op->nc;
+        const int kp = op->kp;
+        const int64_t N = op->geom->N;
+        auto cluster_of_row = [&](int64_t row, int& region_base) -> int {
+            if (row < op->row_xhat) { region_base = -1; return -1; }
+            if (row < op->row_yhat) { region_base = 0; return (int)((row - op->row_xhat) / kp); }
+            region_base = nc;
+            return (int)((row - op->row_yhat) / kp);
+        };
+        std::vector<int32_t> leaf_at(N + 1, -1);
+        for (int c = 0; c < nc; ++c)
+            if (op->child0[c] < 0) leaf_at[op->start[c]] = c;
+        std::vector<char> zero(nc, 0);
+        producers.resize((size_t)reg_base + 3 * nc, 0);
+        for (const Pass& p : op->passes) {
+            for (const Segment& sg0 : p.seg) {
+                Item it{};
+                it.fs.s = sg0;
+                it.fs.kind = p.kind;
+                it.fs.op = (int32_t)oi;
+                it.fs.s.chunk0 = (int32_t)out.chunk.size();
+                double mac64 = 0.0, mac32 = 0.0, bytes = 0.0;
+                for (int q = 0; q < sg0.nchunks; ++q) {
+                    Chunk ch = p.chunk[(size_t)sg0.chunk0 + q];
+                    const int32_t pbase = (int32_t)out.piece.size();
+                    bytes += ch.bytes;
+                    for (int u = 0; u < ch.npieces; ++u) {
+                        const Piece pc = p.piece[(size_t)ch.piece0 + u];
+                        out.piece.push_back(pc);
+                        (pc.type == PIECE_F64 ? mac64 : mac32) += (double)sg0.nrows * pc.ncols * r;
+                        int rb;
+                        const int c = cluster_of_row(pc.in_row, rb);
+                        if (c >= 0) {
+                            const int32_t reg = reg_base + rb + c;
+                            if (std::find(it.deps.begin(), it.deps.end(), reg) == it.deps.end())
+                                it.deps.push_back(reg);
+                        }
+                    }
+                    ch.piece0 = pbase;
+                    out.chunk.push_back(ch);
+                }
+                it.cost = fm.seg_ns + fm.chunk_ns * sg0.nchunks +
+                          std::max({mac64 / fm.f64_per_ns, mac32 / fm.f32_per_ns, bytes / fm.bytes_per_ns});
+                if (sg0.mode == SEG_FINAL || sg0.mode == SEG_FINAL_ADD) {
+                    const int c = leaf_at[sg0.out_row];
+                    if (sg0.mode == SEG_FINAL) it.fs.signal = reg_base + 2 * nc + c;
+                    else {
+                        it.fs.signal = -1;
+                        it.deps.push_back(reg_base + 2 * nc + c);   // after the near field of the leaf
+                    }
+                } else {
                     int rb;
-                    const int c = cluster_of_row(pc.in_row, rb);
-                    if (c >= 0) {
-                        const int32_t reg = rb + c;
-                        if (std::find(it.deps.begin(), it.deps.end(), reg) == it.deps.end())
-                            it.deps.push_back(reg);
+                    const int c = cluster_of_row(sg0.out_row, rb);
+                    it.fs.signal = reg_base + rb + c;
+                    if (rb == nc) {   // y-hat: every producer accumulates atomically
+                        it.fs.s.mode = SEG_ATOMIC;
+                        zero[c] = 1;
                     }
                 }
-                ch.piece0 = pbase;
-                op->fchunk.push_back(ch);
+                if (it.fs.signal >= 0) producers[it.fs.signal]++;
+                items.push_back(std::move(it));
             }
-            it.cost = fm.seg_ns + fm.chunk_ns * sg0.nchunks +
-                      std::max({mac64 / fm.f64_per_ns, mac32 / fm.f32_per_ns, bytes / fm.bytes_per_ns});
-            if (sg0.mode == SEG_FINAL || sg0.mode == SEG_FINAL_ADD) {
-                const int c = leaf_at[sg0.out_row];
-                if (sg0.mode == SEG_FINAL) it.fs.signal = 2 * nc + c;
-                else {
-                    it.fs.signal = -1;
-                    it.deps.push_back(2 * nc + c);   // after the near field of the leaf
-                }
-            } else {
-                int rb;
-                const int c = cluster_of_row(sg0.out_row, rb);
-                it.fs.signal = rb + c;
-                if (rb == nc) {   // y-hat: every producer accumulates atomically
-                    it.fs.s.mode = SEG_ATOMIC;
-                    zero[c] = 1;
-                }
-            }
-            if (it.fs.signal >= 0) op->fexpect[it.fs.signal]++;
-            items.push_back(std::move(it));
         }
+        for (int c = 0; c < nc; ++c)
+            if (zero[c]) out.zero_rows[oi].push_back((int32_t)(op->row_yhat + (int64_t)c * kp));
+        reg_base += 3 * nc;
     }
-    const int nreg = 3 * nc;
+    const int nreg = reg_base;
     const int n = (int)items.size();
     // consumers of every region
     std::vector<std::vector<int32_t>> consumers(nreg);
     for (int i = 0; i < n; ++i)
         for (int32_t d : items[i].deps) consumers[d].push_back(i);
-    // longest path to the end: the passes are listed in a topological order,
-    // so one sweep in reverse settles every consumer before its producers
+    // longest path to the end: every operator's passes are listed in a
+    // topological order, so one sweep in reverse settles every consumer before
+    // its producers
     std::vector<double> reg_blevel(nreg, 0.0);
     for (int i = n - 1; i >= 0; --i) {
         Item& it = items[i];
@@ -438,7 +442,7 @@ double build_flow(h2_handle* op, const FlowModel& fm) {
         for (int32_t d : it.deps) reg_blevel[d] = std::max(reg_blevel[d], it.blevel);
     }
     // list scheduling on `workers` simulated CTAs
-    std::vector<int32_t> reg_left(op->fexpect.begin(), op->fexpect.end());
+    std::vector<int32_t> reg_left(producers);
     std::vector<double> reg_done(nreg, 0.0);
     std::vector<int32_t> deps_left(n);
     std::vector<double> ready_at(n, 0.0);
@@ -471,7 +475,7 @@ double build_flow(h2_handle* op, const FlowModel& fm) {
             pick = pending.top().second;
             pending.pop();
         } else {
-            return -1.0;   // a region that never completes: keep the level-wise launches
+            return -1.0;   // a region that never completes: no dataflow form
         }
         const double start = std::max(t, ready_at[pick]);
         const double fin = start + items[pick].cost;
@@ -490,22 +494,34 @@ double build_flow(h2_handle* op, const FlowModel& fm) {
         }
     }
     // every writer warp of the kernel signals a finished segment
-    std::fill(op->fexpect.begin(), op->fexpect.end(), 0);
+    out.expect.assign(nreg, 0);
     for (const Item& it : items)
         if (it.fs.signal >= 0)
-            op->fexpect[it.fs.signal] +=
-                segment_writers(it.fs.s.nrows, piece_tc(op->fchunk[it.fs.s.chunk0].type0));
+            out.expect[it.fs.signal] += segment_writers(it.fs.s.nrows, piece_tc(out.chunk[it.fs.s.chunk0].type0));
     for (int32_t i : order) {
         Item& it = items[i];
-        it.fs.dep0 = (int32_t)op->fdeps.size();
+        it.fs.dep0 = (int32_t)out.deps.size();
         it.fs.ndep = (int32_t)it.deps.size();
-        for (int32_t d : it.deps) op->fdeps.push_back(d);
-        op->fseg.push_back(it.fs);
+        for (int32_t d : it.deps) out.deps.push_back(d);
+        out.seg.push_back(it.fs);
     }
-    for (int c = 0; c < nc; ++c)
-        if (zero[c]) op->fzero_rows.push_back((int32_t)(op->row_yhat + (int64_t)c * kp));
-    op->use_flow = 1;
+    out.nreg = nreg;
     return makespan * 1e-3;
+}
+
+double build_flow(h2_handle* op, const FlowModel& fm) {
+    FlowOut o;
+    op->use_flow = 0;
+    const double ms = build_flow_multi({op}, fm, o);
+    if (ms < 0.0) return ms;   // keep the level-wise launches
+    op->fseg = std::move(o.seg);
+    op->fchunk = std::move(o.chunk);
+    op->fpiece = std::move(o.piece);
+    op->fdeps = std::move(o.deps);
+    op->fexpect = std::move(o.expect);
+    op->fzero_rows = std::move(o.zero_rows[0]);
+    op->use_flow = 1;
+    return ms;
 }
 
 }  // namespace h2
