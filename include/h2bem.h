@@ -78,7 +78,8 @@ typedef struct {
     int32_t precision;      /* h2_precision                                           */
     int32_t max_rhs;        /* largest r accepted by h2_matvec (workspace size), >= 1 */
     int32_t schedule;       /* h2_schedule: how one h2_matvec is launched              */
-    int32_t reserved[3];    /* must be zero                                           */
+    int32_t autotune;       /* 1: h2_assemble ends with h2_autotune(op, max_rhs)       */
+    int32_t reserved[2];    /* must be zero                                           */
 } h2_params;
 
 /* H2_SCHEDULE_FLOW (default): one persistent kernel after the input gather;
@@ -149,6 +150,27 @@ int h2_matvec_batched(h2_handle* const* ops, int32_t n_ops, const double* const*
  * device); make it before any stream capture.  Every call shares the array:
  * calls whose executions overlap on the GPU race and give wrong results. */
 int h2_matvec_noalloc(h2_handle* op, const double* u1, double* u2, int32_t r, void* cuda_stream);
+
+/* Launch configuration of an operator's product, as chosen by h2_autotune. */
+typedef struct {
+    int32_t schedule;       /* h2_schedule                                            */
+    int32_t stages;         /* shared-memory stages of the segment kernel             */
+    int32_t ctas_per_sm;    /* resident CTAs per SM                                    */
+    int32_t n_candidates;   /* configurations timed                                   */
+    double ms_best;         /* mean time of one product in the chosen configuration   */
+    double ms_default;      /* the same with the configuration h2_assemble chose      */
+} h2_tuning_t;
+
+/* Autotuner of the product's launch configuration (not part of the method: a
+ * property of this implementation).  Times, with CUDA events on `cuda_stream`
+ * and products of r right-hand sides on zero-filled scratch vectors, every
+ * combination of the schedule (the single dataflow launch or one launch per
+ * pass), 2..4 shared-memory stages and 1..max resident CTAs per SM that fits,
+ * keeps the fastest for later h2_matvec calls (the dataflow ticket order is
+ * rebuilt for its CTA count) and reports it in *out (may be NULL).  The
+ * matrices, their layout and the results do not change.  Allocates and frees
+ * its scratch vectors; synchronous.  1 <= r <= max_rhs. */
+int h2_autotune(h2_handle* op, int32_t r, void* cuda_stream, h2_tuning_t* out);
 
 /* Counts and sizes of an operator (Section "Results", "Data compression":
  * storage of the compressed operator and the compression ratio

@@ -40,7 +40,15 @@ class Params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("leaf", ctypes.c_int32), ("eta", ctypes.c_double),
                 ("box_inflation", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("max_rhs", ctypes.c_int32), ("schedule", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("stages", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("n_candidates", ctypes.c_int32), ("ms_best", ctypes.c_double), ("ms_default", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class Stats(ctypes.Structure):
@@ -83,6 +91,7 @@ def load(path: str | None = None):
         L.h2_matvec_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
         L.h2_matvec_batched.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_vp),
                                         ctypes.POINTER(_vp), _c_i32, _vp]
+        L.h2_autotune.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.POINTER(Tuning)]
         L.h2_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
         L.h2_get_tree.argtypes = [_vp] + [_c_i32] * 7 + [_c_d]
         L.h2_get_blocks.argtypes = [_vp] + [_c_i32] * 4
@@ -90,6 +99,7 @@ def load(path: str | None = None):
         L.h2_device_status.argtypes = [_vp]
         L.h2_free.argtypes = [_vp]
         for f in ("h2_build_geometry", "h2_assemble", "h2_matvec", "h2_matvec_noalloc", "h2_matvec_batched",
+                  "h2_autotune",
                   "h2_stats", "h2_get_tree",
                   "h2_get_blocks", "h2_get_psi", "h2_device_status", "h2_free"):
             getattr(L, f).restype = ctypes.c_int
@@ -156,6 +166,13 @@ def h2_matvec_noalloc(op: int, u1_ptr: int, u2_ptr: int, r: int, stream=None) ->
     """u2 = M u1 on device pointers with the library's fixed scratch (no device allocation)."""
     _check(lib().h2_matvec_noalloc(op, u1_ptr, u2_ptr, int(r), _stream_ptr(stream)),
            "h2_matvec_noalloc")
+
+
+def h2_autotune(op: int, r: int, stream=None) -> dict:
+    """Times the launch configurations of an operator's product and keeps the fastest."""
+    t = Tuning()
+    _check(lib().h2_autotune(op, int(r), _stream_ptr(stream), ctypes.byref(t)), "h2_autotune")
+    return t.as_dict()
 
 
 def h2_matvec_batched(ops, u1_ptrs, u2_ptrs, rs, stream=None) -> None:
@@ -253,12 +270,17 @@ class Operator:
 
     def __init__(self, geom: Geometry, m: int = 4, leaf: int = 64, eta: float = 2.0,
                  rho: float = 0.25, precision: int = FP64, max_rhs: int = 1,
-                 schedule: int = SCHEDULE_FLOW):
+                 schedule: int = SCHEDULE_FLOW, autotune: bool = False):
         self.geom = geom
         self.N = geom.N
         self.params = h2_default_params(m=m, leaf=leaf, eta=eta, box_inflation=rho,
-                                        precision=precision, max_rhs=max_rhs, schedule=schedule)
+                                        precision=precision, max_rhs=max_rhs, schedule=schedule,
+                                        autotune=1 if autotune else 0)
         self.handle = h2_assemble(geom.handle, self.params)
+
+    def autotune(self, r: int | None = None, stream=None) -> dict:
+        """Picks the fastest launch configuration for products of r right-hand sides."""
+        return h2_autotune(self.handle, r or self.params.max_rhs, stream)
 
     def stats(self) -> dict:
         return h2_stats(self.handle)

@@ -24,6 +24,7 @@ void free_device(h2_handle* h) {
         f(h->d_xyz); f(h->d_tri); f(h->d_adj_ptr); f(h->d_adj); f(h->d_psi);
     } else {
         h2::release_graph(h);
+        if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
         h2::release_profile(h);
         for (h2::Pass& p : h->passes) { f(p.d_seg); f(p.d_chunk); f(p.d_piece); }
         f(h->d_arena); f(h->d_perm); f(h->d_box); f(h->d_ws); f(h->d_ws32); f(h->d_gather_src);
@@ -125,7 +126,8 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
         p.precision < H2_FP64 || p.precision > H2_BF16X3 ||
         (p.schedule != H2_SCHEDULE_FLOW && p.schedule != H2_SCHEDULE_LEVELS))
         return H2_ERR_INVALID_ARG;
-    for (int i = 0; i < 3; ++i)
+    if (p.autotune != 0 && p.autotune != 1) return H2_ERR_INVALID_ARG;
+    for (int i = 0; i < 2; ++i)
         if (p.reserved[i] != 0) return H2_ERR_INVALID_ARG;
     const auto t0 = std::chrono::steady_clock::now();
     h2_handle* geom = const_cast<h2_handle*>(geom_c);
@@ -145,10 +147,11 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
     h2::build_block_partition(op);
     h2::build_plan(op);
     int rc = H2_OK;
-    if (p.schedule == H2_SCHEDULE_FLOW) {
+    if (p.schedule == H2_SCHEDULE_FLOW || p.autotune) {   // the autotuner may pick either schedule
         h2::FlowModel fm;
         rc = h2::flow_model(op, fm);
         if (rc == H2_OK) op->flow_makespan_us = h2::build_flow(op, fm);
+        if (p.schedule == H2_SCHEDULE_LEVELS) op->use_flow = 0;
     }
     if (rc == H2_OK) rc = h2::upload_plan(op);
     if (rc == H2_OK) rc = h2::assemble_device(op, nullptr);
@@ -156,10 +159,24 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
         release(op);
         return rc;
     }
+    if (p.autotune) {
+        rc = h2::autotune(op, p.max_rhs, nullptr, nullptr);
+        if (rc != H2_OK) {
+            release(op);
+            return rc;
+        }
+    }
     op->assemble_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out_op = op;
     return H2_OK;
+}
+
+int h2_autotune(h2_handle* op, int32_t r, void* cuda_stream, h2_tuning_t* out) {
+    if (!op) return H2_ERR_INVALID_ARG;
+    if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
+    if (r < 1 || r > op->params.max_rhs) return H2_ERR_INVALID_ARG;
+    return h2::autotune(op, r, (cudaStream_t)cuda_stream, out);
 }
 
 int h2_matvec(h2_handle* op, const double* u1, double* u2, int32_t r, void* cuda_stream) {

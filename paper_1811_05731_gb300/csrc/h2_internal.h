@@ -222,13 +222,20 @@ struct h2_handle {
     int stage_bytes = 32768;
     int coupling_split = 4;           // far blocks per coupling segment
     double flow_makespan_us = 0.0;    // simulated duration of the dataflow order
-    // CUDA graph of one matvec (rebuilt when r changes)
+    // CUDA graph of one matvec (the gather and the product launches), captured
+    // on the second call with the same buffers and r, replayed afterwards
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t capture_stream = nullptr;
     int graph_r = 0;
     const double* graph_u1 = nullptr;
     double* graph_u2 = nullptr;
-    cudaGraphNode_t node_first = nullptr, node_last = nullptr;
+    int graph_seen = 0;               // direct calls with the current (u1, u2, r)
+    int graph_fail = 0;               // capture failed once: launch directly from now on
+    // launch configuration chosen by the autotuner (0: defaults)
+    int tune_stages = 0;              // shared-memory stages of the segment kernel
+    int tune_ctas = 0;                // resident CTAs per SM (cap below the occupancy limit)
+    double tune_ms = 0.0;
     int n_launches = 0;
     // single-launch dataflow form
     std::vector<h2::FlowSeg> fseg;
@@ -288,6 +295,7 @@ int flow_model(h2_handle* op, FlowModel& fm);   // CTAs and rates of the device
 int matvec_batched(h2_handle* const* ops, int n, const double* const* u1, double* const* u2, const int32_t* r,
                    cudaStream_t s);
 void drop_batch_plans(uint64_t serial);   // forget the plans that use an operator
+int autotune(h2_handle* op, int r, cudaStream_t s, h2_tuning_t* out);
 }  // namespace h2
 
 #define H2_CUDA_TRY(call)                                        \

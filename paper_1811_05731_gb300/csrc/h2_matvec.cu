@@ -882,7 +882,14 @@ __global__ void k_prologue(const double* __restrict__ u1, double* __restrict__ w
 // Shared-memory stages of the segment kernel for r <= rt right-hand sides: two
 // 32 KB stages let three CTAs share an SM at small r (measured faster than three
 // stages with two CTAs).
-int stages_for(int rt) { return 2 + 0 * rt; }
+int stages_for(int rt) {
+    (void)rt;
+    return 2;
+}
+// The operator's stage count: the autotuner's choice, else the default.
+static int op_stages(const h2_handle* op, int rt) {
+    return op && op->tune_stages > 0 ? op->tune_stages : stages_for(rt);
+}
 
 int rt_for(int r) {
     int rt = 1;
@@ -920,12 +927,13 @@ int ctas_per_sm(F* kernel, size_t smem, int& cached, size_t& cached_smem) {
 // Launches `nsm` x (resident CTAs per SM) CTAs (at most one per segment);
 // *launched receives the grid size.
 template <int RT, bool FLOW, bool TC>
-cudaError_t launch_seg_rt(const KArgs& a, int nsm, size_t smem, cudaStream_t s, int* launched) {
+cudaError_t launch_seg_rt(const KArgs& a, int nsm, size_t smem, cudaStream_t s, int* launched, int cap) {
     static size_t configured = 0, occ_smem = 0;
     static int occ = 0;
     cudaError_t e = set_smem(k_seg<RT, FLOW, TC>, smem, configured);
     if (e != cudaSuccess) return e;
-    const int per_sm = ctas_per_sm(k_seg<RT, FLOW, TC>, smem, occ, occ_smem);
+    int per_sm = ctas_per_sm(k_seg<RT, FLOW, TC>, smem, occ, occ_smem);
+    if (cap > 0 && cap < per_sm) per_sm = cap;   // the autotuner's CTA count
     const int g = std::max(1, std::min(a.nseg, nsm * per_sm));
     if (launched) *launched = g;
     KArgs b = a;
@@ -960,21 +968,22 @@ int seg_occupancy(size_t smem) {
 }
 
 template <bool FLOW, bool TC>
-cudaError_t launch_seg_tc(const KArgs& a, int rt, int nsm, size_t smem, cudaStream_t s, int* launched) {
+cudaError_t launch_seg_tc(const KArgs& a, int rt, int nsm, size_t smem, cudaStream_t s, int* launched, int cap) {
     switch (rt) {
-        case 1: return launch_seg_rt<1, FLOW, TC>(a, nsm, smem, s, launched);
-        case 2: return launch_seg_rt<2, FLOW, TC>(a, nsm, smem, s, launched);
-        case 4: return launch_seg_rt<4, FLOW, TC>(a, nsm, smem, s, launched);
-        case 8: return launch_seg_rt<8, FLOW, TC>(a, nsm, smem, s, launched);
-        case 16: return launch_seg_rt<16, FLOW, TC>(a, nsm, smem, s, launched);
-        default: return launch_seg_rt<32, FLOW, TC>(a, nsm, smem, s, launched);
+        case 1: return launch_seg_rt<1, FLOW, TC>(a, nsm, smem, s, launched, cap);
+        case 2: return launch_seg_rt<2, FLOW, TC>(a, nsm, smem, s, launched, cap);
+        case 4: return launch_seg_rt<4, FLOW, TC>(a, nsm, smem, s, launched, cap);
+        case 8: return launch_seg_rt<8, FLOW, TC>(a, nsm, smem, s, launched, cap);
+        case 16: return launch_seg_rt<16, FLOW, TC>(a, nsm, smem, s, launched, cap);
+        default: return launch_seg_rt<32, FLOW, TC>(a, nsm, smem, s, launched, cap);
     }
 }
 
 template <bool FLOW>
-cudaError_t launch_seg(const KArgs& a, int rt, int nsm, size_t smem, cudaStream_t s, int* launched) {
-    return a.tc ? launch_seg_tc<FLOW, true>(a, rt, nsm, smem, s, launched)
-                : launch_seg_tc<FLOW, false>(a, rt, nsm, smem, s, launched);
+cudaError_t launch_seg(const KArgs& a, int rt, int nsm, size_t smem, cudaStream_t s, int* launched,
+                       int cap = 0) {
+    return a.tc ? launch_seg_tc<FLOW, true>(a, rt, nsm, smem, s, launched, cap)
+                : launch_seg_tc<FLOW, false>(a, rt, nsm, smem, s, launched, cap);
 }
 
 template <class T>
@@ -996,8 +1005,8 @@ static int tc_b_bytes(const h2_handle* op) {
 
 // Shared memory of the segment kernel with `sets` tensor-core operand sets of
 // `alo` + 2 `b` bytes.
-static size_t seg_smem_raw(int rt, int stage_bytes, int alo, int b, int sets) {
-    const size_t S = (size_t)stages_for(rt);
+static size_t seg_smem_raw(int rt, int stages, int stage_bytes, int alo, int b, int sets) {
+    const size_t S = (size_t)stages;
     const size_t red = (size_t)red_buffers(rt) * sizeof(double) * kConsumers * rt;
     const size_t tc = (size_t)sets * ((size_t)alo + 2 * (size_t)b);
     const size_t mid = red_buffers(rt) == 1 ? std::max(red, tc) : red + tc;
@@ -1006,14 +1015,14 @@ static size_t seg_smem_raw(int rt, int stage_bytes, int alo, int b, int sets) {
 
 // Two operand sets (chunk n+1 is prepared while the tensor core multiplies
 // chunk n) when they fit in a CTA's shared memory, else one.
-static int tc_sets_raw(int rt, int stage_bytes, int alo, int b) {
-    return seg_smem_raw(rt, stage_bytes, alo, b, 2) <= (size_t)220 * 1024 ? 2 : 1;
+static int tc_sets_raw(int rt, int stages, int stage_bytes, int alo, int b) {
+    return seg_smem_raw(rt, stages, stage_bytes, alo, b, 2) <= (size_t)220 * 1024 ? 2 : 1;
 }
 static size_t seg_smem_bytes(const h2_handle* op, int rt, int sets) {
-    return seg_smem_raw(rt, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op), sets);
+    return seg_smem_raw(rt, op_stages(op, rt), op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op), sets);
 }
 static int tc_sets_for(const h2_handle* op, int rt) {
-    return tc_sets_raw(rt, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op));
+    return tc_sets_raw(rt, op_stages(op, rt), op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op));
 }
 
 // Launches the gather kernel and every pass (level-wise) or the flow kernel
@@ -1054,7 +1063,7 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
     a.ctx[0] = OpCtx{op->d_arena, ws, ws32, u2, op->d_perm, N, r, 0};
     a.err = op->d_err;
     a.r = r;
-    a.stages = stages_for(rt);
+    a.stages = op_stages(op, rt);
     a.stage_bytes = op->stage_bytes;
     a.tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
     a.tc_alo_bytes = tc_alo_bytes(op);
@@ -1069,7 +1078,7 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
         a.cnt = op->d_fcnt;
         a.nseg = (int)op->fseg.size();
         a.nreg = 3 * op->nc;
-        H2_CUDA_TRY(launch_seg<true>(a, rt, op->nsm, smem, s, &op->flow_grid));
+        H2_CUDA_TRY(launch_seg<true>(a, rt, op->nsm, smem, s, &op->flow_grid, op->tune_ctas));
         H2_CUDA_TRY(mark());
         return H2_OK;
     }
@@ -1078,7 +1087,7 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
         a.chunk = p.d_chunk;
         a.piece = p.d_piece;
         a.nseg = (int)p.seg.size();
-        H2_CUDA_TRY(launch_seg<false>(a, rt, op->nsm, smem, s, &p.grid));
+        H2_CUDA_TRY(launch_seg<false>(a, rt, op->nsm, smem, s, &p.grid, op->tune_ctas));
         H2_CUDA_TRY(mark());
     }
     return H2_OK;
@@ -1090,7 +1099,7 @@ size_t pass_smem_bytes(const h2_handle* op, int rt) { return seg_smem_bytes(op, 
 
 // Resident CTAs and per-CTA rates of the dataflow kernel on the current
 // device for the operator's largest r (input of the ticket-order simulation).
-static int flow_model_raw(int rt, bool tc, size_t smem, int r, FlowModel& fm) {
+static int flow_model_raw(int rt, bool tc, size_t smem, int r, FlowModel& fm, int cap = 0) {
     int dev = 0, nsm = 0, khz = 0;
     H2_CUDA_TRY(cudaGetDevice(&dev));
     H2_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -1105,6 +1114,7 @@ static int flow_model_raw(int rt, bool tc, size_t smem, int r, FlowModel& fm) {
         default: occ = tc ? seg_occupancy<32, true>(smem) : seg_occupancy<32, false>(smem); break;
     }
     const double ghz = khz > 0 ? khz * 1e-6 : 2.07;
+    if (cap > 0 && cap < occ) occ = cap;
     fm.workers = nsm * occ;
     fm.r = r;
     fm.f64_per_ns = 2.0 * ghz / occ;
@@ -1116,7 +1126,7 @@ static int flow_model_raw(int rt, bool tc, size_t smem, int r, FlowModel& fm) {
 int flow_model(h2_handle* op, FlowModel& fm) {
     const int rt = rt_for(op->params.max_rhs);
     const bool tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
-    return flow_model_raw(rt, tc, pass_smem_bytes(op, rt), op->params.max_rhs, fm);
+    return flow_model_raw(rt, tc, pass_smem_bytes(op, rt), op->params.max_rhs, fm, op->tune_ctas);
 }
 
 // Checks, on the host, the invariants the bulk copies rely on (16-byte aligned
@@ -1148,6 +1158,24 @@ static int validate_chunks(const h2_handle* op, const std::vector<Segment>* segs
     return H2_OK;
 }
 
+// (Re)uploads the dataflow arrays of an operator (its ticket order may have
+// been rebuilt by the autotuner).
+static int upload_flow(h2_handle* op) {
+    for (void** p : {(void**)&op->d_fseg, (void**)&op->d_fchunk, (void**)&op->d_fpiece, (void**)&op->d_fdeps,
+                     (void**)&op->d_fexpect, (void**)&op->d_fzero_rows})
+        if (*p) {
+            cudaFree(*p);
+            *p = nullptr;
+        }
+    int rc;
+    if ((rc = upload_vec(op->fseg, &op->d_fseg)) || (rc = upload_vec(op->fchunk, &op->d_fchunk)) ||
+        (rc = upload_vec(op->fpiece, &op->d_fpiece)) || (rc = upload_vec(op->fdeps, &op->d_fdeps)) ||
+        (rc = upload_vec(op->fexpect, &op->d_fexpect)) || (rc = upload_vec(op->fzero_rows, &op->d_fzero_rows)))
+        return rc;
+    if (!op->d_fcnt) H2_CUDA_TRY(cudaMalloc((void**)&op->d_fcnt, sizeof(int32_t) * (3 * (size_t)op->nc + 1)));
+    return H2_OK;
+}
+
 int upload_plan(h2_handle* op) {
     for (const Pass& p : op->passes) {
         if (validate_chunks(op, &p.seg, p.chunk, p.piece) != H2_OK) {
@@ -1173,14 +1201,7 @@ int upload_plan(h2_handle* op) {
     }
     op->nsm = nsm;
     if ((rc = upload_vec(op->zero_rows, &op->d_zero_rows))) return rc;
-    if (op->use_flow) {
-        if ((rc = upload_vec(op->fseg, &op->d_fseg)) || (rc = upload_vec(op->fchunk, &op->d_fchunk)) ||
-            (rc = upload_vec(op->fpiece, &op->d_fpiece)) || (rc = upload_vec(op->fdeps, &op->d_fdeps)) ||
-            (rc = upload_vec(op->fexpect, &op->d_fexpect)) ||
-            (rc = upload_vec(op->fzero_rows, &op->d_fzero_rows)))
-            return rc;
-        H2_CUDA_TRY(cudaMalloc((void**)&op->d_fcnt, sizeof(int32_t) * (3 * (size_t)op->nc + 1)));
-    }
+    if (op->use_flow && (rc = upload_flow(op))) return rc;
     if ((rc = upload_vec(op->gather_src, &op->d_gather_src))) return rc;
     H2_CUDA_TRY(cudaMalloc((void**)&op->d_ws, sizeof(double) * (size_t)op->ws_rows * op->params.max_rhs));
     if (op->params.precision != H2_FP64)
@@ -1197,6 +1218,9 @@ void release_graph(h2_handle* op) {
     op->graph_exec = nullptr;
     op->graph = nullptr;
     op->graph_r = 0;
+    op->graph_u1 = nullptr;
+    op->graph_u2 = nullptr;
+    op->graph_seen = 0;
 }
 
 void release_profile(h2_handle* op) {
@@ -1224,11 +1248,160 @@ int read_profile(h2_handle* op, std::vector<double>& ms, int& ncalls) {
     return H2_OK;
 }
 
+// One product on device buffers.  A product with the same (u1, u2, r) as the
+// previous call is captured into a CUDA graph (on the operator's own capture
+// stream) and replayed from then on; products while the caller's stream is
+// itself being captured, while profiling, or after a failed capture are
+// launched directly.
 int matvec_device(h2_handle* op, const double* u1, double* u2, int r, cudaStream_t s) {
-    std::vector<cudaEvent_t> ev;
-    int rc = launch_matvec(op, u1, u2, r, s, op->d_ws, op->d_ws32, op->use_flow != 0,
-                           op->prof_enabled ? &ev : nullptr, &op->prof_pool);
-    if (op->prof_enabled) op->prof_calls.push_back(std::move(ev));
+    if (op->prof_enabled) {
+        std::vector<cudaEvent_t> ev;
+        int rc = launch_matvec(op, u1, u2, r, s, op->d_ws, op->d_ws32, op->use_flow != 0, &ev, &op->prof_pool);
+        op->prof_calls.push_back(std::move(ev));
+        return rc;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;
+    }
+    if (cs == cudaStreamCaptureStatusNone && !op->graph_fail) {
+        const bool same = op->graph_u1 == u1 && op->graph_u2 == u2 && op->graph_r == r;
+        if (same && op->graph_exec) {
+            H2_CUDA_TRY(cudaGraphLaunch(op->graph_exec, s));
+            return H2_OK;
+        }
+        if (same && op->graph_seen > 0) {
+            bool ok = true;
+            if (!op->capture_stream)
+                ok = cudaStreamCreateWithFlags(&op->capture_stream, cudaStreamNonBlocking) == cudaSuccess;
+            ok = ok && cudaStreamBeginCapture(op->capture_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            int rc = H2_ERR_CUDA;
+            if (ok) {
+                rc = launch_matvec(op, u1, u2, r, op->capture_stream, op->d_ws, op->d_ws32, op->use_flow != 0,
+                                   nullptr, nullptr);
+                cudaGraph_t g = nullptr;
+                ok = cudaStreamEndCapture(op->capture_stream, &g) == cudaSuccess && rc == H2_OK && g;
+                if (ok) ok = cudaGraphInstantiate(&op->graph_exec, g, 0) == cudaSuccess;
+                if (ok) op->graph = g;
+                else if (g) cudaGraphDestroy(g);
+            }
+            if (ok) {
+                H2_CUDA_TRY(cudaGraphLaunch(op->graph_exec, s));
+                return H2_OK;
+            }
+            cudaGetLastError();   // capture did not work here: direct launches from now on
+            op->graph_exec = nullptr;
+            op->graph_fail = 1;
+        } else if (!same) {
+            release_graph(op);
+            op->graph_u1 = u1;
+            op->graph_u2 = u2;
+            op->graph_r = r;
+            op->graph_seen = 1;
+        }
+    }
+    return launch_matvec(op, u1, u2, r, s, op->d_ws, op->d_ws32, op->use_flow != 0, nullptr, nullptr);
+}
+
+// Times one configuration: `iters` products after two unmeasured ones.
+static int time_products(h2_handle* op, const double* x, double* y, int r, cudaStream_t s, int iters,
+                         double* ms) {
+    for (int i = 0; i < 2; ++i) {
+        int rc = launch_matvec(op, x, y, r, s, op->d_ws, op->d_ws32, op->use_flow != 0, nullptr, nullptr);
+        if (rc != H2_OK) return rc;
+    }
+    cudaEvent_t e0, e1;
+    H2_CUDA_TRY(cudaEventCreate(&e0));
+    H2_CUDA_TRY(cudaEventCreate(&e1));
+    H2_CUDA_TRY(cudaEventRecord(e0, s));
+    int rc = H2_OK;
+    for (int i = 0; i < iters && rc == H2_OK; ++i)
+        rc = launch_matvec(op, x, y, r, s, op->d_ws, op->d_ws32, op->use_flow != 0, nullptr, nullptr);
+    H2_CUDA_TRY(cudaEventRecord(e1, s));
+    H2_CUDA_TRY(cudaEventSynchronize(e1));
+    float t = 0.0f;
+    H2_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = (double)t / iters;
+    return rc;
+}
+
+// Ticket order of the dataflow form for the operator's current launch
+// configuration, uploaded.
+static int rebuild_flow(h2_handle* op) {
+    FlowModel fm;
+    int rc = flow_model(op, fm);
+    if (rc != H2_OK) return rc;
+    if (build_flow(op, fm) < 0.0) return H2_ERR_INVALID_ARG;
+    return upload_flow(op);
+}
+
+int autotune(h2_handle* op, int r, cudaStream_t s, h2_tuning_t* out) {
+    const int64_t N = op->geom->N;
+    double *x = nullptr, *y = nullptr;
+    H2_CUDA_TRY(cudaMalloc((void**)&x, sizeof(double) * (size_t)N * r));
+    H2_CUDA_TRY(cudaMalloc((void**)&y, sizeof(double) * (size_t)N * r));
+    H2_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)N * r, s));
+    release_graph(op);
+    const bool have_flow = !op->fseg.empty();
+    const int use_flow0 = op->use_flow, st0 = op->tune_stages, ct0 = op->tune_ctas;
+    double ms0 = 0.0;
+    int rc = time_products(op, x, y, r, s, 1, &ms0);
+    const int iters = std::max(1, std::min(10, (int)(20.0 / std::max(ms0, 1e-3))));
+    if (rc == H2_OK) rc = time_products(op, x, y, r, s, iters, &ms0);
+    int best_flow = use_flow0, best_st = st0, best_ct = ct0, ncand = 0;
+    double best = ms0;
+    const int rt = rt_for(r);
+    const bool tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
+    for (int flow = have_flow ? 1 : 0; flow >= 0 && rc == H2_OK; --flow) {
+        for (int stages = 2; stages <= 4 && rc == H2_OK; ++stages) {
+            op->tune_stages = stages;
+            const size_t smem = pass_smem_bytes(op, rt);
+            if (smem > (size_t)227 * 1024) continue;
+            int occ = 1;
+            switch (rt) {
+                case 1: occ = tc ? seg_occupancy<1, true>(smem) : seg_occupancy<1, false>(smem); break;
+                case 2: occ = tc ? seg_occupancy<2, true>(smem) : seg_occupancy<2, false>(smem); break;
+                case 4: occ = tc ? seg_occupancy<4, true>(smem) : seg_occupancy<4, false>(smem); break;
+                case 8: occ = tc ? seg_occupancy<8, true>(smem) : seg_occupancy<8, false>(smem); break;
+                case 16: occ = tc ? seg_occupancy<16, true>(smem) : seg_occupancy<16, false>(smem); break;
+                default: occ = tc ? seg_occupancy<32, true>(smem) : seg_occupancy<32, false>(smem); break;
+            }
+            for (int cap = 1; cap <= std::min(occ, 4) && rc == H2_OK; ++cap) {
+                op->tune_ctas = cap;
+                op->use_flow = flow;
+                if (flow && (rc = rebuild_flow(op)) != H2_OK) break;
+                double ms = 0.0;
+                rc = time_products(op, x, y, r, s, iters, &ms);
+                ++ncand;
+                if (rc == H2_OK && ms < best) {
+                    best = ms;
+                    best_flow = flow;
+                    best_st = stages;
+                    best_ct = cap;
+                }
+            }
+        }
+    }
+    op->use_flow = best_flow;
+    op->tune_stages = best_st;
+    op->tune_ctas = best_ct;
+    op->tune_ms = best;
+    if (rc == H2_OK && have_flow) rc = rebuild_flow(op);   // the order for the chosen CTA count
+    op->use_flow = best_flow;
+    op->n_launches = op->use_flow ? 2 : 1 + (int)op->passes.size();
+    cudaFree(x);
+    cudaFree(y);
+    if (out) {
+        out->schedule = op->use_flow ? H2_SCHEDULE_FLOW : H2_SCHEDULE_LEVELS;
+        out->stages = op_stages(op, rt);
+        out->ctas_per_sm = op->tune_ctas;
+        out->n_candidates = ncand;
+        out->ms_best = best;
+        out->ms_default = ms0;
+    }
     return rc;
 }
 
@@ -1285,8 +1458,8 @@ int matvec_batched(h2_handle* const* ops, int n, const double* const* u1, double
     }
     const int rt = rt_for(rmax);
     const int stage_bytes = ops[0]->stage_bytes;
-    const int sets = tc ? tc_sets_raw(rt, stage_bytes, alo, b) : 1;
-    const size_t smem = seg_smem_raw(rt, stage_bytes, alo, b, sets);
+    const int sets = tc ? tc_sets_raw(rt, stages_for(rt), stage_bytes, alo, b) : 1;
+    const size_t smem = seg_smem_raw(rt, stages_for(rt), stage_bytes, alo, b, sets);
     std::vector<uint64_t> key(n);
     for (int i = 0; i < n; ++i) key[i] = ops[i]->serial;
     BatchPlan* bp = nullptr;
