@@ -143,8 +143,11 @@ int h2_matvec_batched(h2_handle* const* ops, int32_t n_ops, const double* const*
  *           (independent of max_rhs).  Asynchronous on `cuda_stream`.
  * The workspace is a fixed array of 4,194,304 doubles (32 MiB) inside the
  * library, present on every GPU that loads it until the process exits.
- * Requires (N + 2 * n_clusters * k_even + 2) * r <= 4,194,304, else returns
- * H2_ERR_SCRATCH_LIMIT without launching anything.  No cudaMalloc, cudaFree
+ * It must hold W = rows x r doubles, rows = (the mesh nodes, each leaf
+ * cluster's count rounded up to a multiple of 4) + 2 x n_clusters x k4 + 4
+ * with k4 = m^3 rounded up to a multiple of 4, and for reduced-precision
+ * operators W more floats after a 256-byte boundary; larger problems get
+ * H2_ERR_SCRATCH_LIMIT without anything being launched.  No cudaMalloc, cudaFree
  * or other allocating routine is called.  The first call on a device looks up
  * the array's device address (and loads the library's kernels on that
  * device); make it before any stream capture.  Every call shares the array:
@@ -212,8 +215,20 @@ int h2_get_psi(const h2_handle* h, double* psi);
 
 /* Synchronises the device and reports whether any h2_matvec on `op` since
  * the last call gave up a bounded device-side wait (H2_ERR_TIMEOUT; the
- * result of that product is then undefined).  Clears the flag. */
+ * result of that product is then undefined).  Clears the flag.  While the
+ * flag is set, later dataflow products on `op` stop at their first wait for
+ * another CTA's output (their results are undefined too): read the status
+ * after a product whose result matters. */
 int h2_device_status(h2_handle* op);
+
+/* Failure-detection test hook (not part of the method).  enable = 1 makes
+ * the dataflow product of `op` wait for one more signal of a region than its
+ * producers ever send, so that the waiting CTA's bounded wait (1 s) runs out:
+ * the product stops early, leaves u2 undefined and h2_device_status(op)
+ * returns H2_ERR_TIMEOUT; the CUDA context stays usable.  enable = 0
+ * restores the operator.  Only for operators with the dataflow schedule;
+ * synchronises the device. */
+int h2_fault_inject_stall(h2_handle* op, int32_t enable);
 
 /* Per-pass timing (a measurement aid, not needed for computing).  While
  * enabled, every h2_matvec on `op` records CUDA events on its stream before

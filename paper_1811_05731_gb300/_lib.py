@@ -92,6 +92,7 @@ def load(path: str | None = None):
         L.h2_matvec_batched.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_vp),
                                         ctypes.POINTER(_vp), _c_i32, _vp]
         L.h2_autotune.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.POINTER(Tuning)]
+        L.h2_fault_inject_stall.argtypes = [_vp, ctypes.c_int32]
         L.h2_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
         L.h2_get_tree.argtypes = [_vp] + [_c_i32] * 7 + [_c_d]
         L.h2_get_blocks.argtypes = [_vp] + [_c_i32] * 4
@@ -99,7 +100,7 @@ def load(path: str | None = None):
         L.h2_device_status.argtypes = [_vp]
         L.h2_free.argtypes = [_vp]
         for f in ("h2_build_geometry", "h2_assemble", "h2_matvec", "h2_matvec_noalloc", "h2_matvec_batched",
-                  "h2_autotune",
+                  "h2_autotune", "h2_fault_inject_stall",
                   "h2_stats", "h2_get_tree",
                   "h2_get_blocks", "h2_get_psi", "h2_device_status", "h2_free"):
             getattr(L, f).restype = ctypes.c_int

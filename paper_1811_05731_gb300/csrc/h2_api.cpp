@@ -172,6 +172,24 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
     return H2_OK;
 }
 
+int h2_fault_inject_stall(h2_handle* op, int32_t enable) {
+    if (!op) return H2_ERR_INVALID_ARG;
+    if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
+    if (!op->use_flow || !op->d_fexpect) return H2_ERR_INVALID_ARG;
+    // the first region any segment of the ticket order waits for
+    int32_t reg = -1;
+    for (const h2::FlowSeg& f : op->fseg)
+        if (f.ndep > 0) {
+            reg = op->fdeps[f.dep0];
+            break;
+        }
+    if (reg < 0) return H2_ERR_INVALID_ARG;
+    const int32_t v = op->fexpect[reg] + (enable ? 1 : 0);   // one signal more than ever arrives
+    H2_CUDA_TRY(cudaDeviceSynchronize());
+    H2_CUDA_TRY(cudaMemcpy(op->d_fexpect + reg, &v, sizeof(int32_t), cudaMemcpyHostToDevice));
+    return H2_OK;
+}
+
 int h2_autotune(h2_handle* op, int32_t r, void* cuda_stream, h2_tuning_t* out) {
     if (!op) return H2_ERR_INVALID_ARG;
     if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
