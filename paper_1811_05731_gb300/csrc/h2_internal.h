@@ -26,6 +26,11 @@
 #define H2_MAX_RHS 32
 #define H2_MAX_BATCH 16        // operators of one batched product
 #define H2_MAX_CHUNK_COLS 128   // input columns of one chunk (shared-memory staging)
+
+// Input columns per chunk of an operator built for up to max_rhs right-hand
+// sides: 64 above 8 right-hand sides, so that a stage's input buffer (columns x
+// right-hand sides x 8 bytes) stays at 16 KB and three stages fit at 32.
+inline int chunk_cols_for(int max_rhs) { return max_rhs > 8 ? 64 : H2_MAX_CHUNK_COLS; }
 #define H2_MAX_CHUNK_PIECES 32  // matrices of one chunk (one producer lane each)
 
 namespace h2 {
@@ -221,6 +226,7 @@ struct h2_handle {
     int stages = 3;                   // shared-memory stages of the pass kernel
     int stage_bytes = 32768;
     int coupling_split = 4;           // far blocks per coupling segment
+    int chunk_cols = H2_MAX_CHUNK_COLS;   // input columns per chunk (chunk_cols_for(max_rhs))
     double flow_makespan_us = 0.0;    // simulated duration of the dataflow order
     // CUDA graph of one matvec (the gather and the product launches), captured
     // on the second call with the same buffers and r, replayed afterwards

@@ -147,6 +147,8 @@ struct KArgs {
     int tc_sets;               // operand sets (2: the next chunk is prepared while the tensor core works)
     int tc_cols;               // TMEM columns per CTA (power of 2, at most 512 / resident CTAs per SM)
     int tc_nacc;               // accumulators of the hi*hi products (K steps round-robin)
+    int tc_ncorr;              // accumulators of the correction products (round-robin)
+    int tc_np;                 // accumulator width: right-hand sides rounded up to 16
     int nops;                  // operators of the launch (several: a batched product)
     OpCtx ctx[H2_MAX_BATCH];
 };
@@ -222,15 +224,29 @@ __device__ __forceinline__ void issue_inputs(const OpCtx& c, const SPiece* pc, i
     }
 }
 
+// Error-free FP32 addition (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
 // Multiplies the pieces of one staged chunk into the thread's accumulators.
+// FP64 chunks add into `acc`.  FP32 chunks (far-field matrices, leaf bases)
+// stay on the FP32 pipe, which GB300 runs at 64 times the FP64 rate: the
+// chunk's products are summed in FP32; in a segment with FP32 output
+// (`packed`) each accumulator register pair holds a compensated FP32 sum
+// (hi word: sum, lo word: the TwoSum error terms), which the segment end
+// converts once; otherwise the chunk's sum is added to the FP64 accumulator.
+// With r == RT the inputs of one column are read as 16-byte vectors.
 template <int RT>
 __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const SPiece* pieces, int npieces,
                                               bool f32, const unsigned char* xin, int r, int nrows, int row,
-                                              int g, int G, double (&acc)[RT]) {
-    for (int p = 0; p < npieces; ++p) {
-        const SPiece P = pieces[p];
-        const int nc = P.ncols;
-        if (!f32) {
+                                              int g, int G, bool packed, double (&acc)[RT]) {
+    if (!f32) {
+        for (int p = 0; p < npieces; ++p) {
+            const SPiece P = pieces[p];
+            const int nc = P.ncols;
             const double* A = reinterpret_cast<const double*>(stage + P.smem_off) + row;
             const double* x = reinterpret_cast<const double*>(xin + P.xoff);
             if (RT == 1) {
@@ -243,6 +259,18 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const 
                 }
                 if (col < nc) a0 = fma(A[col * nrows], x[col], a0);
                 acc[0] += a0 + a1;
+            } else if (r == RT) {   // 16-byte aligned rows of RT values
+#pragma unroll 2
+                for (int col = g; col < nc; col += G) {
+                    const double v = A[col * nrows];
+                    const double2* x2 = reinterpret_cast<const double2*>(x + col * RT);
+#pragma unroll
+                    for (int c = 0; c < RT / 2; ++c) {
+                        const double2 xv = x2[c];
+                        acc[2 * c] = fma(v, xv.x, acc[2 * c]);
+                        acc[2 * c + 1] = fma(v, xv.y, acc[2 * c + 1]);
+                    }
+                }
             } else {
 #pragma unroll 2
                 for (int col = g; col < nc; col += G) {
@@ -252,35 +280,77 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const 
                         if (c < r) acc[c] = fma(v, x[col * r + c], acc[c]);
                 }
             }
-        } else {
-            const float* A = reinterpret_cast<const float*>(stage + P.smem_off) + row;
-            const float* x = reinterpret_cast<const float*>(xin + P.xoff);
-            if (RT == 1) {
-                float a0 = 0.0f, a1 = 0.0f;
-                int col = g;
+        }
+        return;
+    }
+    float acc32[RT];
+#pragma unroll
+    for (int c = 0; c < RT; ++c) acc32[c] = 0.0f;
+    for (int p = 0; p < npieces; ++p) {
+        const SPiece P = pieces[p];
+        const int nc = P.ncols;
+        const float* A = reinterpret_cast<const float*>(stage + P.smem_off) + row;
+        const float* x = reinterpret_cast<const float*>(xin + P.xoff);
+        if (RT == 1) {
+            float a0 = 0.0f, a1 = 0.0f;
+            int col = g;
 #pragma unroll 4
-                for (; col + G < nc; col += 2 * G) {
-                    a0 = fmaf(A[col * nrows], x[col], a0);
-                    a1 = fmaf(A[(col + G) * nrows], x[col + G], a1);
-                }
-                if (col < nc) a0 = fmaf(A[col * nrows], x[col], a0);
-                acc[0] += (double)(a0 + a1);
-            } else {
-                float acc32[RT];
-#pragma unroll
-                for (int c = 0; c < RT; ++c) acc32[c] = 0.0f;
+            for (; col + G < nc; col += 2 * G) {
+                a0 = fmaf(A[col * nrows], x[col], a0);
+                a1 = fmaf(A[(col + G) * nrows], x[col + G], a1);
+            }
+            if (col < nc) a0 = fmaf(A[col * nrows], x[col], a0);
+            acc32[0] += a0 + a1;
+        } else if (RT % 4 == 0 && r == RT) {   // 16-byte aligned rows of RT values
 #pragma unroll 2
-                for (int col = g; col < nc; col += G) {
-                    const float v = A[col * nrows];
+            for (int col = g; col < nc; col += G) {
+                const float v = A[col * nrows];
+                const float4* x4 = reinterpret_cast<const float4*>(x + col * RT);
 #pragma unroll
-                    for (int c = 0; c < RT; ++c)
-                        if (c < r) acc32[c] = fmaf(v, x[col * r + c], acc32[c]);
+                for (int c = 0; c < RT / 4; ++c) {
+                    const float4 xv = x4[c];
+                    acc32[4 * c] = fmaf(v, xv.x, acc32[4 * c]);
+                    acc32[4 * c + 1] = fmaf(v, xv.y, acc32[4 * c + 1]);
+                    acc32[4 * c + 2] = fmaf(v, xv.z, acc32[4 * c + 2]);
+                    acc32[4 * c + 3] = fmaf(v, xv.w, acc32[4 * c + 3]);
                 }
+            }
+        } else {
+#pragma unroll 2
+            for (int col = g; col < nc; col += G) {
+                const float v = A[col * nrows];
 #pragma unroll
-                for (int c = 0; c < RT; ++c) acc[c] += (double)acc32[c];
+                for (int c = 0; c < RT; ++c)
+                    if (c < r) acc32[c] = fmaf(v, x[col * r + c], acc32[c]);
             }
         }
     }
+    if (packed) {
+#pragma unroll
+        for (int c = 0; c < RT; ++c) {
+            float s, e;
+            two_sum(__int_as_float(__double2hiint(acc[c])), acc32[c], s, e);
+            const float l = __int_as_float(__double2loint(acc[c])) + e;
+            acc[c] = __hiloint2double(__float_as_int(s), __float_as_int(l));
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < RT; ++c) acc[c] += (double)acc32[c];
+    }
+}
+
+// Sum of the G packed compensated FP32 partial sums of one output value
+// (see consume_chunk), in FP32 with TwoSum: no FP64 arithmetic.
+__device__ __forceinline__ float packed_sum(const double* red, int stride, int G) {
+    float s = 0.0f, e = 0.0f;
+    for (int g2 = 0; g2 < G; ++g2) {
+        const double d = red[g2 * stride];
+        float t, u;
+        two_sum(s, __int_as_float(__double2hiint(d)), t, u);
+        s = t;
+        e += u + __int_as_float(__double2loint(d));
+    }
+    return s + e;
 }
 
 // Writer warps of a segment: warp w < writer_warps(nrows) adds the G partial
@@ -297,24 +367,23 @@ __device__ __forceinline__ void write_segment(const StageDesc& D, const double* 
     if (rr >= nrows) return;
     const bool fin = D.mode == SEG_FINAL || D.mode == SEG_FINAL_ADD;
     const int64_t orow = fin ? (int64_t)perm[D.out_row + rr] : (int64_t)(D.out_row + rr) * r;
+    if (D.out_f32) {   // packed FP32 partial sums, FP32 output
+        for (int c = 0; c < r; ++c) {
+            const float v = packed_sum(red + rr * RT + c, nrows * RT, G);
+            float* dst = ws32 + orow + c;
+            if (D.mode == SEG_STORE) *dst = v;
+            else if (D.mode == SEG_ADD) *dst = __ldcg(dst) + v;
+            else atomicAdd(dst, v);
+        }
+        return;
+    }
     for (int c = 0; c < r; ++c) {
         double s = 0.0;
         for (int g2 = 0; g2 < G; ++g2) s += red[(g2 * nrows + rr) * RT + c];
-        if (fin) {
-            double* dst = u2 + (int64_t)c * N + orow;
-            if (D.mode == SEG_FINAL) *dst = s;
-            else *dst = __ldcg(dst) + s;
-        } else if (D.out_f32) {
-            float* dst = ws32 + orow + c;
-            if (D.mode == SEG_STORE) *dst = (float)s;
-            else if (D.mode == SEG_ADD) *dst = __ldcg(dst) + (float)s;
-            else atomicAdd(dst, (float)s);
-        } else {
-            double* dst = ws + orow + c;
-            if (D.mode == SEG_STORE) *dst = s;
-            else if (D.mode == SEG_ADD) *dst = __ldcg(dst) + s;
-            else atomicAdd(dst, s);
-        }
+        double* dst = fin ? u2 + (int64_t)c * N + orow : ws + orow + c;
+        if (D.mode == SEG_STORE || D.mode == SEG_FINAL) *dst = s;
+        else if (D.mode == SEG_ADD || D.mode == SEG_FINAL_ADD) *dst = __ldcg(dst) + s;
+        else atomicAdd(dst, s);
     }
 }
 
@@ -329,10 +398,10 @@ __device__ __forceinline__ void write_segment(const StageDesc& D, const double* 
 // BF16: the tiles already hold hi and lo), build the
 // K-major B operand (the chunk's input vectors, N = r padded to the MMA's
 // granularity, hi and lo), and one thread issues, per K step, the three
-// products hi*hi + hi*lo + lo*hi into an FP32 accumulator in tensor memory
-// (M = 64 or 128 rows).  The accumulator lives across the chunks of a
-// segment; at its end the four warps that own the TMEM lane quarters read it
-// out (row i of an M = 128 tile is lane i; rows 16q..16q+15 of an M = 64 tile
+// products hi*hi + hi*lo + lo*hi into FP32 accumulators in tensor memory
+// (M = 64 or 128 rows).  The accumulators live across the chunks of a
+// segment; at its end the four warps that own the TMEM lane quarters read and
+// add them (row i of an M = 128 tile is lane i; rows 16q..16q+15 of an M = 64 tile
 // are lanes 32q..32q+15) and write the segment.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -371,10 +440,12 @@ __device__ __forceinline__ int b_offset(int n, int kk, int Np, int es) {
     return (kk / per) * (Np / 8) * 128 + (n / 8) * 128 + (n % 8) * 16 + (kk % per) * es;
 }
 
-// Input buffer of one stage: at most kMaxChunkCols FP64 rows of RT values
+// Input columns a stage holds for r <= rt (see chunk_cols_for).
+__host__ __device__ constexpr int xin_cols(int rt) { return rt > 8 ? 64 : kMaxChunkCols; }
+// Input buffer of one stage: at most xin_cols(RT) FP64 rows of RT values
 // plus the 16-byte rounding of every piece.
 __host__ __device__ constexpr size_t xin_bytes(int rt) {
-    return sizeof(double) * kMaxChunkCols * rt + 16 * H2_MAX_CHUNK_PIECES;
+    return sizeof(double) * xin_cols(rt) * rt + 16 * H2_MAX_CHUNK_PIECES;
 }
 
 // Partial-sum buffers of the segment kernel: two (alternating between
@@ -424,8 +495,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                                                              : red_span + tc_span));
     uint64_t* empty = full + S;
     uint64_t* segbar = empty + S;
-    uint64_t* cbar = segbar + 1;     // consumers: tensor operands ready
-    uint64_t* mmabar = cbar + 1;     // [2]: tensor-core products of chunk n done (barrier n & 1)
+    uint64_t* cbar = segbar + 1;     // [2]: tensor operands of chunk n ready (barrier n & 1)
+    uint64_t* mmabar = cbar + 2;     // [2]: tensor-core products of chunk n done (barrier n & 1)
     __shared__ StageDesc sd[kMaxStages];
     __shared__ SPiece spc[kMaxStages][H2_MAX_CHUNK_PIECES];
     __shared__ int abort_flag;
@@ -439,7 +510,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
             mbar_init(&empty[s], kConsumers);
         }
         mbar_init(segbar, kConsumers);
-        mbar_init(cbar, kConsumers);
+        mbar_init(&cbar[0], kConsumers - 32);   // the operand writers: consumer warps 1..7
+        mbar_init(&cbar[1], kConsumers - 32);
         mbar_init(&mmabar[0], 1);
         mbar_init(&mmabar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -582,20 +654,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
         }
     } else {
         // ---------------- consumer warps ----------------
-        double acc[RT];
+        double acc[RT];   // FP64 sums, or packed compensated FP32 sums (segments with FP32 output)
 #pragma unroll
         for (int c = 0; c < RT; ++c) acc[c] = 0.0;
-        uint32_t segphase = 0, cphase = 0;
+        uint32_t segphase = 0;
         int tcn = 0;            // tensor-core chunks so far
         int segk = 0;           // K steps of the current tensor-core segment issued so far
         int pend_st = -1;       // stage of the last tensor-core chunk, released once its products are done
         int pend_n = 0;
-        // zero padding of B (right-hand sides r..Np-1) is written once when the
-        // operand sets do not share memory with the partial sums
-        const bool pad_once = NRED == 2;
-        if (TC && pad_once)
-            for (int q = tid; q < (int)(tc_span / 16); q += kConsumers)
-                reinterpret_cast<float4*>(tc_base)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         auto release_pending = [&]() -> bool {
             if (!TC || pend_st < 0) return true;
             if (!mbar_wait_or_abort(&mmabar[pend_n & 1], (uint32_t)(pend_n >> 1) & 1u, abortp)) return false;
@@ -632,12 +698,15 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                 }
                 unsigned char* set = tc_base + (size_t)(tcn % a.tc_sets) * tc_set_bytes;
                 unsigned char* t_alo = set;
-                unsigned char* t_bhi = set + a.tc_alo_bytes;
-                unsigned char* t_blo = t_bhi + a.tc_b_bytes;
-                if (type == PIECE_TF32) {   // A = hi (in place) + lo, both nearest TF32 values
+                unsigned char* t_b = set + a.tc_alo_bytes;   // B: 2 Np rows, hi parts then lo parts
+                const int N2 = 2 * Np;
+                // operands: written by consumer warps 1..7 while warp 0 issues the
+                // previous chunk's products
+                const int wt = tid - 32, nwt = kConsumers - 32;
+                if (type == PIECE_TF32 && wt >= 0) {   // A = hi (in place) + lo, both nearest TF32 values
                     float4* A4 = reinterpret_cast<float4*>(stg);
                     float4* L4 = reinterpret_cast<float4*>(t_alo);
-                    for (int q = tid; q < D.cbytes / 16; q += kConsumers) {
+                    for (int q = wt; q < D.cbytes / 16; q += nwt) {
                         const float4 v = A4[q];
                         const float4 h = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
                         A4[q] = h;
@@ -645,23 +714,26 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                                             tf32_rn(v.w - h.w));
                     }
                 }
-                // B operand: rows n < Np (right-hand sides), K = the pieces' input rows
-                // (each piece padded to whole K steps with zeros).  A work unit is one
+                // B operand: rows n < r (right-hand sides, hi parts) and Np + n (lo
+                // parts), K = the pieces' input rows (each piece padded to whole K steps
+                // with zeros).  Rows r..Np-1 and Np+r..2Np-1 are not written: they only
+                // reach accumulator columns that are never read.  A work unit is one
                 // 16-byte core row: right-hand side n, `per` consecutive K rows (8 BF16
                 // or 4 TF32 values), written with one vector store per part.
-                {
+                if (wt >= 0) {
                     const int per = 16 / bes;
-                    const int nb = pad_once ? r : Np;   // right-hand sides written per chunk
+                    const int nb = r;
                     int kb = 0;
                     for (int p = 0; p < D.npieces; ++p) {
                         const SPiece P = spc[st][p];
                         const int kp = (P.ncols + ks - 1) / ks * ks;
                         const float* xp = reinterpret_cast<const float*>(xin + P.xoff);
                         const int units = (kp / per) * nb;
-                        for (int u = tid; u < units; u += kConsumers) {
+                        for (int u = wt; u < units; u += nwt) {
                             const int kg = u / nb, n = u - kg * nb;   // K group, right-hand side
                             const int j0 = kg * per;
-                            const int off = b_offset(n, kb + j0, Np, bes);
+                            const int off = b_offset(n, kb + j0, N2, bes);
+                            const int offl = b_offset(Np + n, kb + j0, N2, bes);
                             if (type == PIECE_TF32) {
                                 float h[4], l[4];
 #pragma unroll
@@ -670,8 +742,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                                     h[e] = tf32_rn(x);
                                     l[e] = tf32_rn(x - h[e]);
                                 }
-                                *reinterpret_cast<float4*>(t_bhi + off) = make_float4(h[0], h[1], h[2], h[3]);
-                                *reinterpret_cast<float4*>(t_blo + off) = make_float4(l[0], l[1], l[2], l[3]);
+                                *reinterpret_cast<float4*>(t_b + off) = make_float4(h[0], h[1], h[2], h[3]);
+                                *reinterpret_cast<float4*>(t_b + offl) = make_float4(l[0], l[1], l[2], l[3]);
                             } else {
                                 __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
@@ -680,63 +752,74 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                                     h[e] = __float2bfloat16_rn(x);
                                     l[e] = __float2bfloat16_rn(x - __bfloat162float(h[e]));
                                 }
-                                *reinterpret_cast<uint4*>(t_bhi + off) = *reinterpret_cast<const uint4*>(h);
-                                *reinterpret_cast<uint4*>(t_blo + off) = *reinterpret_cast<const uint4*>(l);
+                                *reinterpret_cast<uint4*>(t_b + off) = *reinterpret_cast<const uint4*>(h);
+                                *reinterpret_cast<uint4*>(t_b + offl) = *reinterpret_cast<const uint4*>(l);
                             }
                         }
                         kb += kp;
                     }
                 }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(cbar);
-                if (!mbar_wait_or_abort(cbar, cphase++ & 1u, abortp)) {
-                    atomicExch(a.err, 1);
-                    abort_flag = 1;
-                    break;
+                if (wt >= 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_arrive(&cbar[tcn & 1]);
                 }
                 // K steps of this chunk (every consumer thread tracks the segment's count)
                 int csteps = 0;
                 for (int p = 0; p < D.npieces; ++p) csteps += (spc[st][p].ncols + ks - 1) / ks;
                 if (tid == 0) {
-                    // hi*hi of K step g goes to accumulator g % nacc, the two
-                    // correction products of every step to accumulator nacc: few
-                    // tensor-core accumulations per FP32 accumulator
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t idesc = mma_idesc(type, Mp, Np);
-                    const uint32_t lboA = 16u * Mp, lboB = (uint32_t)(Np / 8) * 128u;
-                    const int bper = 16 / bes;
-                    const int nacc = a.tc_nacc;
-                    const uint32_t tcorr = tmem_base + (uint32_t)(nacc * Np);
-                    // descriptors advance by adding (byte offset >> 4) to their
-                    // 14-bit start-address field (shared memory < 256 KB: no carry)
-                    const uint64_t dA0 = smem_desc(smem_addr(stg), lboA, 128);
-                    const uint64_t dL0 = type == PIECE_TF32 ? smem_desc(smem_addr(t_alo), lboA, 128)
-                                                            : dA0 + (uint64_t)((32u * Mp) >> 4);
-                    const uint64_t dBh = smem_desc(smem_addr(t_bhi), lboB, 128);
-                    const uint64_t dBl = smem_desc(smem_addr(t_blo), lboB, 128);
-                    const uint64_t a_step = (uint64_t)((ks * Mp * 4) >> 4);        // one K slab of A
-                    const uint64_t b_step = (uint64_t)(((ks / bper) * lboB) >> 4);  // one K step of B
-                    int gstep = segk;
-                    int accn = segk % nacc;
-                    uint64_t bo = 0;
-                    for (int p = 0; p < D.npieces; ++p) {
-                        const SPiece P = spc[st][p];
-                        const int nst = (P.ncols + ks - 1) / ks;
-                        uint64_t ao = (uint64_t)(P.smem_off >> 4);
-                        for (int q = 0; q < nst; ++q, ++gstep, ao += a_step, bo += b_step) {
-                            const uint32_t tacc = tmem_base + (uint32_t)(accn * Np);
-                            mma_issue(type, tacc, dA0 + ao, dBh + bo, idesc, gstep >= nacc ? 1u : 0u);
-                            mma_issue(type, tcorr, dA0 + ao, dBl + bo, idesc, gstep > 0 ? 1u : 0u);
-                            mma_issue(type, tcorr, dL0 + ao, dBh + bo, idesc, 1u);
-                            if (++accn == nacc) accn = 0;
+                    // Per K step two products: A_hi x [B_hi | B_lo] (N = 2 Np: the hi*hi
+                    // and hi*lo parts side by side) into accumulator pair g % nacc, and
+                    // A_lo x B_hi (N = Np) into correction accumulator g % ncorr.  One
+                    // tcgen05.mma costs about the same for any N up to 128, so the
+                    // merged product saves a third of the instructions; products into
+                    // one accumulator wait for each other, into different ones overlap.
+                    bool ok = mbar_wait_or_abort(&cbar[tcn & 1], (uint32_t)(tcn >> 1) & 1u, abortp);
+                    if (!ok) {
+                        atomicExch(a.err, 1);
+                        abort_flag = 1;
+                    } else {
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t idesc2 = mma_idesc(type, Mp, N2), idesc1 = mma_idesc(type, Mp, Np);
+                        const uint32_t lboA = 16u * Mp, lboB = (uint32_t)(N2 / 8) * 128u;
+                        const int bper = 16 / bes;
+                        const int nacc = a.tc_nacc, ncorr = a.tc_ncorr;
+                        const uint32_t pair_cols = 2u * (uint32_t)a.tc_np;
+                        const uint32_t tcorr0 = tmem_base + (uint32_t)nacc * pair_cols;
+                        // descriptors advance by adding (byte offset >> 4) to their
+                        // 14-bit start-address field (shared memory < 256 KB: no carry)
+                        const uint64_t dA0 = smem_desc(smem_addr(stg), lboA, 128);
+                        const uint64_t dL0 = type == PIECE_TF32 ? smem_desc(smem_addr(t_alo), lboA, 128)
+                                                                : dA0 + (uint64_t)((32u * Mp) >> 4);
+                        const uint64_t dB = smem_desc(smem_addr(t_b), lboB, 128);
+                        const uint64_t a_step = (uint64_t)((ks * Mp * 4) >> 4);        // one K slab of A
+                        const uint64_t b_step = (uint64_t)(((ks / bper) * lboB) >> 4);  // one K step of B
+                        int gstep = segk;
+                        int accn = segk % nacc, corn = segk % ncorr;
+                        uint64_t bo = 0;
+                        for (int p = 0; p < D.npieces; ++p) {
+                            const SPiece P = spc[st][p];
+                            const int nst = (P.ncols + ks - 1) / ks;
+                            uint64_t ao = (uint64_t)(P.smem_off >> 4);
+                            for (int k2 = 0; k2 < nst; ++k2, ++gstep, ao += a_step, bo += b_step) {
+                                mma_issue(type, tmem_base + (uint32_t)accn * pair_cols, dA0 + ao, dB + bo, idesc2,
+                                          gstep >= nacc ? 1u : 0u);
+                                mma_issue(type, tcorr0 + (uint32_t)(corn * a.tc_np), dL0 + ao, dB + bo, idesc1,
+                                          gstep >= ncorr ? 1u : 0u);
+                                if (++accn == nacc) accn = 0;
+                                if (++corn == ncorr) corn = 0;
+                            }
                         }
                     }
+                    // committed also after an abort, so that the bounded waits on it end
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                      smem_addr(&mmabar[tcn & 1]))
                                  : "memory");
                 }
+                if (*abortp) break;
                 segk += csteps;
-                const int nused = segk < a.tc_nacc ? segk : a.tc_nacc;   // hi*hi accumulators written
+                // accumulators written: hi pairs, then correction ones
+                const int nused = segk < a.tc_nacc ? segk : a.tc_nacc;
+                const int ncused = segk < a.tc_ncorr ? segk : a.tc_ncorr;
                 // the previous chunk's products are done by now in the common case
                 if (!release_pending()) {
                     atomicExch(a.err, 1);
@@ -758,8 +841,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                         float* dst = C.ws32 + (int64_t)(D.out_row + (row < 0 ? 0 : row)) * r;
                         for (int c0 = 0; c0 < Np; c0 += 8) {   // 8 right-hand sides at a time
                             float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                            for (int j = 0; j <= nused; ++j) {   // nused hi*hi accumulators, then the corrections
-                                const uint32_t col = (uint32_t)((j < nused ? j : a.tc_nacc) * Np + c0);
+                            // the hi*hi and hi*lo halves of the pairs, then the corrections
+                            for (int j = 0; j < 2 * nused + ncused; ++j) {
+                                const uint32_t col = (uint32_t)(j < 2 * nused ? (j >> 1) * 2 * a.tc_np + (j & 1) * Np + c0
+                                                                              : a.tc_nacc * 2 * a.tc_np +
+                                                                                    (j - 2 * nused) * a.tc_np + c0);
                                 uint32_t v[8];
                                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                                              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]),
@@ -802,13 +888,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
             const int row = tid % nrows, g = tid / nrows;
             if (g < G)
                 consume_chunk<RT>(stage_base + (size_t)st * a.stage_bytes, spc[st], D.npieces, D.f32 != 0,
-                                  xbase + (size_t)st * kXin, r, nrows, row, g, G, acc);
+                                  xbase + (size_t)st * kXin, r, nrows, row, g, G, D.out_f32 != 0, acc);
             mbar_arrive(&empty[st]);
             if (D.last) {
                 double* rb = red + (size_t)(segphase % NRED) * kConsumers * RT;
                 if (g < G) {
 #pragma unroll
-                    for (int c = 0; c < RT; ++c) rb[tid * RT + c] = acc[c];
+                    for (int c = 0; c < RT; ++c) rb[tid * RT + c] = acc[c];   // packed sums as they are
                 }
 #pragma unroll
                 for (int c = 0; c < RT; ++c) acc[c] = 0.0;
@@ -879,16 +965,13 @@ __global__ void k_prologue(const double* __restrict__ u1, double* __restrict__ w
     for (int64_t idx = i0; idx < nclear; idx += stride) clear[idx] = 0;
 }
 
-// Shared-memory stages of the segment kernel for r <= rt right-hand sides: two
-// 32 KB stages let three CTAs share an SM at small r (measured faster than three
-// stages with two CTAs).
-int stages_for(int rt) {
-    (void)rt;
-    return 2;
-}
+int stages_for(int rt, int stage_bytes, int alo, int b);
+static int tc_alo_bytes(const h2_handle* op);
+static int tc_b_bytes(const h2_handle* op);
 // The operator's stage count: the autotuner's choice, else the default.
 static int op_stages(const h2_handle* op, int rt) {
-    return op && op->tune_stages > 0 ? op->tune_stages : stages_for(rt);
+    return op && op->tune_stages > 0 ? op->tune_stages
+                                     : stages_for(rt, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op));
 }
 
 int rt_for(int r) {
@@ -940,12 +1023,16 @@ cudaError_t launch_seg_rt(const KArgs& a, int nsm, size_t smem, cudaStream_t s, 
     if (TC) {
         // TMEM columns per CTA: a power of 2 such that the resident CTAs of an SM
         // never ask for more than its 512 columns (an allocation never waits);
-        // the hi*hi accumulators fill them after one for the corrections
-        int cols = 256;
+        // half of the accumulators take the hi*hi products, half the corrections
+        int cols = 512;
         while (cols * per_sm > 512 && cols > 32) cols >>= 1;
         const int np = (a.r + 15) / 16 * 16;
+        // hi accumulator pairs of 2 np columns and correction accumulators of np
+        if (cols < 3 * np) return cudaErrorInvalidConfiguration;
         b.tc_cols = cols;
-        b.tc_nacc = std::max(1, std::min(8, cols / np - 1));
+        b.tc_np = np;
+        b.tc_nacc = std::max(1, std::min(8, cols / (4 * np)));
+        b.tc_ncorr = std::max(1, std::min(8, (cols - 2 * np * b.tc_nacc) / np));
     }
     k_seg<RT, FLOW, TC><<<g, kBlock, smem, s>>>(b);
     return cudaGetLastError();
@@ -1010,7 +1097,19 @@ static size_t seg_smem_raw(int rt, int stages, int stage_bytes, int alo, int b, 
     const size_t red = (size_t)red_buffers(rt) * sizeof(double) * kConsumers * rt;
     const size_t tc = (size_t)sets * ((size_t)alo + 2 * (size_t)b);
     const size_t mid = red_buffers(rt) == 1 ? std::max(red, tc) : red + tc;
-    return S * (size_t)stage_bytes + S * xin_bytes(rt) + mid + sizeof(uint64_t) * (2 * S + 4);
+    return S * (size_t)stage_bytes + S * xin_bytes(rt) + mid + sizeof(uint64_t) * (2 * S + 5);
+}
+
+// Shared-memory stages of the segment kernel for r <= rt right-hand sides.
+// Small r: two 32 KB stages, so that three CTAs share an SM (measured faster
+// than three stages with two CTAs).  Large r (one CTA per SM): as many stages
+// as fit (up to kMaxStages), so that the next chunks' copies are in flight
+// while a chunk is multiplied and its predecessor's tensor-core products end.
+int stages_for(int rt, int stage_bytes, int alo, int b) {
+    if (rt <= 8) return 2;
+    int S = 2;
+    while (S < kMaxStages && seg_smem_raw(rt, S + 1, stage_bytes, alo, b, 1) <= (size_t)220 * 1024) ++S;
+    return S;
 }
 
 // Two operand sets (chunk n+1 is prepared while the tensor core multiplies
@@ -1031,6 +1130,7 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
                   float* ws32, bool flow, std::vector<cudaEvent_t>* marks,
                   std::vector<cudaEvent_t>* pool) {
     const int rt = rt_for(r);
+    if ((int64_t)op->chunk_cols * r > (int64_t)xin_cols(rt) * rt) return H2_ERR_INVALID_ARG;   // stage inputs
     const size_t smem = pass_smem_bytes(op, rt);
     const int64_t N = op->geom->N;
     auto mark = [&]() -> cudaError_t {
@@ -1137,7 +1237,7 @@ static int validate_chunks(const h2_handle* op, const std::vector<Segment>* segs
                            const std::vector<Piece>& pieces) {
     for (const Chunk& c : chunks) {
         if (c.src % 16 || c.bytes % 16 || c.bytes <= 0 || c.bytes > op->stage_bytes || c.npieces < 1 ||
-            c.npieces > H2_MAX_CHUNK_PIECES || c.ncols < 1 || c.ncols > kMaxChunkCols ||
+            c.npieces > H2_MAX_CHUNK_PIECES || c.ncols < 1 || c.ncols > op->chunk_cols ||
             c.src + c.bytes > op->arena_bytes || (size_t)c.piece0 + c.npieces > pieces.size())
             return H2_ERR_INVALID_ARG;
         int cols = 0;
@@ -1150,11 +1250,21 @@ static int validate_chunks(const h2_handle* op, const std::vector<Segment>* segs
         }
         if (cols != c.ncols || pieces[c.piece0].in_row != c.in_row0 || pieces[c.piece0].type != c.type0)
             return H2_ERR_INVALID_ARG;
+        for (int q = 1; q < c.npieces; ++q)   // one piece type per chunk
+            if (pieces[(size_t)c.piece0 + q].type != c.type0) return H2_ERR_INVALID_ARG;
     }
     if (segs)
-        for (const Segment& sg : *segs)
+        for (const Segment& sg : *segs) {
             if (sg.nchunks < 1 || sg.nrows < 1 || sg.nrows > H2_MAX_LEAF || (size_t)sg.chunk0 + sg.nchunks > chunks.size())
                 return H2_ERR_INVALID_ARG;
+            // the consumers keep one kind of accumulator per segment: tensor
+            // memory or registers, and packed FP32 sums when the output is FP32
+            const bool tc0 = piece_tc(chunks[sg.chunk0].type0);
+            for (int q = 0; q < sg.nchunks; ++q) {
+                const int t = chunks[(size_t)sg.chunk0 + q].type0;
+                if (piece_tc(t) != tc0 || (sg.out_f32 && t == PIECE_F64)) return H2_ERR_INVALID_ARG;
+            }
+        }
     return H2_OK;
 }
 
@@ -1458,8 +1568,11 @@ int matvec_batched(h2_handle* const* ops, int n, const double* const* u1, double
     }
     const int rt = rt_for(rmax);
     const int stage_bytes = ops[0]->stage_bytes;
-    const int sets = tc ? tc_sets_raw(rt, stages_for(rt), stage_bytes, alo, b) : 1;
-    const size_t smem = seg_smem_raw(rt, stages_for(rt), stage_bytes, alo, b, sets);
+    const int nst = stages_for(rt, stage_bytes, alo, b);
+    const int sets = tc ? tc_sets_raw(rt, nst, stage_bytes, alo, b) : 1;
+    const size_t smem = seg_smem_raw(rt, nst, stage_bytes, alo, b, sets);
+    for (int i = 0; i < n; ++i)   // a stage holds every chunk's inputs
+        if ((int64_t)ops[i]->chunk_cols * r[i] > (int64_t)xin_cols(rt) * rt) return H2_ERR_INVALID_ARG;
     std::vector<uint64_t> key(n);
     for (int i = 0; i < n; ++i) key[i] = ops[i]->serial;
     BatchPlan* bp = nullptr;
@@ -1511,7 +1624,7 @@ int matvec_batched(h2_handle* const* ops, int n, const double* const* u1, double
                          (int)r[i], 0};
     a.err = ops[0]->d_err;
     a.r = rmax;
-    a.stages = stages_for(rt);
+    a.stages = nst;
     a.stage_bytes = stage_bytes;
     a.tc = tc;
     a.tc_alo_bytes = alo;

@@ -82,9 +82,9 @@ void emit_pass(h2_handle* op, const char* name, int32_t kind, std::vector<SegSpe
             m.ref->ncols = m.ncols;
             m.ref->type = m.type;
             p.macs += (int64_t)s.nrows * m.ncols;
-            if (mbytes <= stage && kcols <= H2_MAX_CHUNK_COLS) {
+            if (mbytes <= stage && kcols <= op->chunk_cols) {
                 if (cur.src >= 0 && ((arena + mbytes - cur.src) > stage ||
-                                     cur_cols + m.ncols > H2_MAX_CHUNK_COLS ||
+                                     cur_cols + m.ncols > op->chunk_cols ||
                                      cur.npieces >= H2_MAX_CHUNK_PIECES))
                     close();
                 if (cur.src < 0) {
@@ -111,7 +111,7 @@ void emit_pass(h2_handle* op, const char* name, int32_t kind, std::vector<SegSpe
                 // rows stay 16-byte aligned
                 const int step = tc ? tc_kstep(m.type) : 4;
                 int cols = (int)(stage / col_bytes);
-                cols = std::max(step, std::min(cols, H2_MAX_CHUNK_COLS) / step * step);
+                cols = std::max(step, std::min(cols, op->chunk_cols) / step * step);
                 for (int c0 = 0; c0 < kcols; c0 += cols) {
                     const int cc = std::min(cols, kcols - c0);
                     const int real = std::max(0, std::min(cc, m.ncols - c0));   // input columns
@@ -146,6 +146,7 @@ void emit_pass(h2_handle* op, const char* name, int32_t kind, std::vector<SegSpe
 }  // namespace
 
 void build_plan(h2_handle* op) {
+    op->chunk_cols = chunk_cols_for(op->params.max_rhs);
     const int nc = op->nc;
     const int k = op->k;
     const int kp = op->kp;
