@@ -214,7 +214,7 @@ struct h2_handle {
     int32_t* d_gather_src = nullptr;
     double* d_ws = nullptr;
     float* d_ws32 = nullptr;
-    std::vector<int32_t> zero_rows;   // y-hat regions cleared before the coupling pass
+    std::vector<int32_t> zero_rows;   // x-hat / y-hat regions accumulated atomically (cleared by the gather)
     int32_t* d_zero_rows = nullptr;
     double* d_io = nullptr;           // device staging for host-pointer calls
     int* d_err = nullptr;             // device error word (bounded waits)

@@ -238,11 +238,13 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // (`packed`) each accumulator register pair holds a compensated FP32 sum
 // (hi word: sum, lo word: the TwoSum error terms), which the segment end
 // converts once; otherwise the chunk's sum is added to the FP64 accumulator.
-// With r == RT the inputs of one column are read as 16-byte vectors.
+// With r == RT the inputs of one column are read as 16-byte vectors.  At
+// RT = 1 the FP64 products run in two chains, acc[0] and acc1, which persist
+// over the segment's chunks and meet at its end.
 template <int RT>
 __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const SPiece* pieces, int npieces,
                                               bool f32, const unsigned char* xin, int r, int nrows, int row,
-                                              int g, int G, bool packed, double (&acc)[RT]) {
+                                              int g, int G, bool packed, double (&acc)[RT], double& acc1) {
     if (!f32) {
         for (int p = 0; p < npieces; ++p) {
             const SPiece P = pieces[p];
@@ -250,7 +252,7 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const 
             const double* A = reinterpret_cast<const double*>(stage + P.smem_off) + row;
             const double* x = reinterpret_cast<const double*>(xin + P.xoff);
             if (RT == 1) {
-                double a0 = 0.0, a1 = 0.0;
+                double a0 = acc[0], a1 = acc1;
                 int col = g;
 #pragma unroll 4
                 for (; col + G < nc; col += 2 * G) {
@@ -258,7 +260,8 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const 
                     a1 = fma(A[(col + G) * nrows], x[col + G], a1);
                 }
                 if (col < nc) a0 = fma(A[col * nrows], x[col], a0);
-                acc[0] += a0 + a1;
+                acc[0] = a0;
+                acc1 = a1;
             } else if (r == RT) {   // 16-byte aligned rows of RT values
 #pragma unroll 2
                 for (int col = g; col < nc; col += G) {
@@ -655,6 +658,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
     } else {
         // ---------------- consumer warps ----------------
         double acc[RT];   // FP64 sums, or packed compensated FP32 sums (segments with FP32 output)
+        double acc1 = 0.0;   // second FP64 chain at RT = 1
 #pragma unroll
         for (int c = 0; c < RT; ++c) acc[c] = 0.0;
         uint32_t segphase = 0;
@@ -888,16 +892,18 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
             const int row = tid % nrows, g = tid / nrows;
             if (g < G)
                 consume_chunk<RT>(stage_base + (size_t)st * a.stage_bytes, spc[st], D.npieces, D.f32 != 0,
-                                  xbase + (size_t)st * kXin, r, nrows, row, g, G, D.out_f32 != 0, acc);
+                                  xbase + (size_t)st * kXin, r, nrows, row, g, G, D.out_f32 != 0, acc, acc1);
             mbar_arrive(&empty[st]);
             if (D.last) {
                 double* rb = red + (size_t)(segphase % NRED) * kConsumers * RT;
                 if (g < G) {
 #pragma unroll
                     for (int c = 0; c < RT; ++c) rb[tid * RT + c] = acc[c];   // packed sums as they are
+                    if (RT == 1 && !D.out_f32) rb[tid] = acc[0] + acc1;
                 }
 #pragma unroll
                 for (int c = 0; c < RT; ++c) acc[c] = 0.0;
+                acc1 = 0.0;
                 mbar_arrive(segbar);
                 if (!mbar_wait_or_abort(segbar, segphase++ & 1u, abortp)) {
                     atomicExch(a.err, 1);

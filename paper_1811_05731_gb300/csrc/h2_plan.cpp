@@ -4,7 +4,12 @@
 //
 // The product y = M x is evaluated in passes:
 //   U0      x-hat_s = W_s^T x|_s                    leaves s that need x-hat
-//   U(l)    x-hat_t = sum_children E_c^T x-hat_c    level l = L-2 .. 0 (upward)
+//   U(l)    x-hat_t += E_c^T x-hat_c                level l = L-2 .. 0 (upward), one
+//                                                   segment per child c of t, so that
+//                                                   each starts as soon as x-hat_c is
+//                                                   complete (two atomic additions to
+//                                                   the cleared x-hat_t: exact order
+//                                                   independence)
 //   C       y-hat_t += S_ts x-hat_s                 all admissible blocks
 //   D(l)    y-hat_c (+)= E_c y-hat_parent           level l = 1 .. L-1 (downward)
 //   F       y|_t = V_t y-hat_t + sum_s N_ts x|_s    leaves (near field incl. the
@@ -191,6 +196,7 @@ void build_plan(h2_handle* op) {
     auto xrow = [&](int c) { return (int32_t)(op->row_xhat + (int64_t)c * kp); };
     auto yrow = [&](int c) { return (int32_t)(op->row_yhat + (int64_t)c * kp); };
 
+    op->zero_rows.clear();   // workspace regions accumulated atomically, cleared by the gather
     op->W.assign(nc, MatRef{});
     op->V.assign(nc, MatRef{});
     op->Eup.assign(nc, MatRef{});
@@ -215,31 +221,39 @@ void build_plan(h2_handle* op) {
         }
         emit_pass(op, "up_leaf", PASS_UP_LEAF, segs, arena);
     }
-    // U(l): transfers towards the root
+    // U(l): transfers towards the root, one segment per child
     for (int l = op->nlevels - 2; l >= 0; --l) {
         std::vector<SegSpec> segs;
         for (int c = 0; c < nc; ++c) {
             if (op->level[c] != l || op->child0[c] < 0 || !op->need_x[c]) continue;
-            SegSpec s;
-            s.out_row = xrow(c);
-            s.nrows = k;
-            s.mode = SEG_STORE;
-            for (int ch : {op->child0[c], op->child1[c]})
+            op->zero_rows.push_back(xrow(c));
+            for (int ch : {op->child0[c], op->child1[c]}) {
+                SegSpec s;
+                s.out_row = xrow(c);
+                s.nrows = k;
+                s.mode = SEG_ATOMIC;
                 s.mats.push_back({&op->Eup[ch], k, PT, xrow(ch)});
-            s.bytes = 2LL * k * k;
-            segs.push_back(s);
+                s.bytes = (int64_t)k * k;
+                segs.push_back(s);
+            }
         }
         emit_pass(op, "up_transfer", PASS_UP_TRANSFER, segs, arena);
     }
     // C: coupling, grouped by target and split into groups of at most `split`
-    // blocks (atomic accumulation into the cleared y-hat)
+    // blocks (atomic accumulation into the cleared y-hat); within a target the
+    // blocks are ordered by the level of their source, deepest first (the
+    // order in which the sources' x-hat complete), so that a group does not
+    // hold early sources back behind a late one
     {
         std::vector<std::vector<int32_t>> by_t(nc);
         for (size_t b = 0; b < op->far_t.size(); ++b) by_t[op->far_t[b]].push_back((int32_t)b);
+        for (auto& v : by_t)
+            std::stable_sort(v.begin(), v.end(), [&](int32_t x, int32_t y) {
+                return op->level[op->far_s[x]] > op->level[op->far_s[y]];
+            });
         const int64_t nfar = (int64_t)op->far_t.size();
         const int split = op->coupling_split;
         std::vector<SegSpec> segs;
-        op->zero_rows.clear();
         for (int t = 0; t < nc; ++t) {
             if (by_t[t].empty()) continue;
             op->zero_rows.push_back(yrow(t));
@@ -372,7 +386,7 @@ double build_flow_multi(const std::vector<h2_handle*>& ops, const FlowModel& fm,
         std::vector<int32_t> leaf_at(N + 1, -1);
         for (int c = 0; c < nc; ++c)
             if (op->child0[c] < 0) leaf_at[op->start[c]] = c;
-        std::vector<char> zero(nc, 0);
+        std::vector<char> zero(2 * nc, 0);   // x-hat (c) and y-hat (nc + c) regions written atomically
         producers.resize((size_t)reg_base + 3 * nc, 0);
         for (const Pass& p : op->passes) {
             for (const Segment& sg0 : p.seg) {
@@ -416,6 +430,8 @@ double build_flow_multi(const std::vector<h2_handle*>& ops, const FlowModel& fm,
                     it.fs.signal = reg_base + rb + c;
                     if (rb == nc) {   // y-hat: every producer accumulates atomically
                         it.fs.s.mode = SEG_ATOMIC;
+                        zero[nc + c] = 1;
+                    } else if (it.fs.s.mode == SEG_ATOMIC) {
                         zero[c] = 1;
                     }
                 }
@@ -424,7 +440,9 @@ double build_flow_multi(const std::vector<h2_handle*>& ops, const FlowModel& fm,
             }
         }
         for (int c = 0; c < nc; ++c)
-            if (zero[c]) out.zero_rows[oi].push_back((int32_t)(op->row_yhat + (int64_t)c * kp));
+            if (zero[c]) out.zero_rows[oi].push_back((int32_t)(op->row_xhat + (int64_t)c * kp));
+        for (int c = 0; c < nc; ++c)
+            if (zero[nc + c]) out.zero_rows[oi].push_back((int32_t)(op->row_yhat + (int64_t)c * kp));
         reg_base += 3 * nc;
     }
     const int nreg = reg_base;
