@@ -357,13 +357,13 @@ __device__ __forceinline__ float packed_sum(const double* red, int stride, int G
 }
 
 // Writer warps of a segment: warp w < writer_warps(nrows) adds the G partial
-// sums of rows 32w .. 32w+31 (one row per lane, all r right-hand sides) and
-// writes them; the other consumer warps go on with the next chunk.
+// sums of rows 32w .. 32w+31 (one row per lane) for right-hand sides c0 ..
+// c0+cn-1, stored in `red` with stride `rs` per thread, and writes them; the
+// other consumer warps go on with the next chunk.
 __host__ __device__ constexpr int writer_warps(int nrows) { return (nrows + 31) / 32; }
 
-template <int RT>
-__device__ __forceinline__ void write_segment(const StageDesc& D, const double* red, int r, int G,
-                                              double* ws, float* ws32, double* u2,
+__device__ __forceinline__ void write_segment(const StageDesc& D, const double* red, int rs, int c0, int cn, int r,
+                                              int G, double* ws, float* ws32, double* u2,
                                               const int32_t* __restrict__ perm, int64_t N) {
     const int nrows = D.nrows;
     const int rr = threadIdx.x;   // writer warps only: threadIdx.x < 32 * writer_warps(nrows)
@@ -371,19 +371,19 @@ __device__ __forceinline__ void write_segment(const StageDesc& D, const double* 
     const bool fin = D.mode == SEG_FINAL || D.mode == SEG_FINAL_ADD;
     const int64_t orow = fin ? (int64_t)perm[D.out_row + rr] : (int64_t)(D.out_row + rr) * r;
     if (D.out_f32) {   // packed FP32 partial sums, FP32 output
-        for (int c = 0; c < r; ++c) {
-            const float v = packed_sum(red + rr * RT + c, nrows * RT, G);
-            float* dst = ws32 + orow + c;
+        for (int c = 0; c < cn; ++c) {
+            const float v = packed_sum(red + rr * rs + c, nrows * rs, G);
+            float* dst = ws32 + orow + c0 + c;
             if (D.mode == SEG_STORE) *dst = v;
             else if (D.mode == SEG_ADD) *dst = __ldcg(dst) + v;
             else atomicAdd(dst, v);
         }
         return;
     }
-    for (int c = 0; c < r; ++c) {
+    for (int c = 0; c < cn; ++c) {
         double s = 0.0;
-        for (int g2 = 0; g2 < G; ++g2) s += red[(g2 * nrows + rr) * RT + c];
-        double* dst = fin ? u2 + (int64_t)c * N + orow : ws + orow + c;
+        for (int g2 = 0; g2 < G; ++g2) s += red[(g2 * nrows + rr) * rs + c];
+        double* dst = fin ? u2 + (int64_t)(c0 + c) * N + orow : ws + orow + c0 + c;
         if (D.mode == SEG_STORE || D.mode == SEG_FINAL) *dst = s;
         else if (D.mode == SEG_ADD || D.mode == SEG_FINAL_ADD) *dst = __ldcg(dst) + s;
         else atomicAdd(dst, s);
@@ -454,11 +454,14 @@ __host__ __device__ constexpr size_t xin_bytes(int rt) {
 // Partial-sum buffers of the segment kernel: two (alternating between
 // segments, so one barrier per segment suffices) while they are small.
 __host__ __device__ constexpr int red_buffers(int rt) { return rt <= 8 ? 2 : 1; }
+// Right-hand sides per reduction round: all of them up to 8, else rounds of 8
+// (two consumer barriers per round), which keeps the buffer at 16 KB.
+__host__ __device__ constexpr int red_rhs(int rt) { return rt <= 8 ? rt : 8; }
 
 // Shared-memory layout of the segment kernel (dynamic part):
 //   stages x stage_bytes             matrix chunks (bulk copies)
 //   stages x xin_bytes(RT)           the chunks' input values
-//   red_buffers x kConsumers*RT*8    partial sums of the row groups
+//   red_buffers x kConsumers*red_rhs(RT)*8   partial sums of the row groups
 //   tc_alo_bytes, 2 x tc_b_bytes     tensor-core operands (TF32 lo parts, B hi / lo)
 //   stages x 2 + 3 mbarriers         full[], empty[], segment, operands-ready, products-done
 //
@@ -481,6 +484,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
     const int S = a.stages;
     constexpr size_t kXin = xin_bytes(RT);
     constexpr int NRED = red_buffers(RT);
+    constexpr int RR = red_rhs(RT);
     unsigned char* stage_base = smem;
     unsigned char* xbase = smem + (size_t)S * a.stage_bytes;
     double* red = reinterpret_cast<double*>(xbase + (size_t)S * kXin);
@@ -489,9 +493,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
     // before the next chunk is prepared)
     // operand set q: [lo parts of A][B hi][B lo] at tc_base + q * tc_set_bytes
     unsigned char* tc_base = NRED == 1 ? reinterpret_cast<unsigned char*>(red)
-                                       : reinterpret_cast<unsigned char*>(red + NRED * kConsumers * RT);
+                                       : reinterpret_cast<unsigned char*>(red + NRED * kConsumers * RR);
     const size_t tc_set_bytes = (size_t)a.tc_alo_bytes + 2 * (size_t)a.tc_b_bytes;
-    const size_t red_span = (size_t)NRED * kConsumers * RT * sizeof(double);
+    const size_t red_span = (size_t)NRED * kConsumers * RR * sizeof(double);
     const size_t tc_span = (size_t)a.tc_sets * tc_set_bytes;
     uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(red) +
                                                   (NRED == 1 ? (red_span > tc_span ? red_span : tc_span)
@@ -895,31 +899,37 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                                   xbase + (size_t)st * kXin, r, nrows, row, g, G, D.out_f32 != 0, acc, acc1);
             mbar_arrive(&empty[st]);
             if (D.last) {
-                double* rb = red + (size_t)(segphase % NRED) * kConsumers * RT;
-                if (g < G) {
+                // partial sums of the row groups, RR right-hand sides per round
+                bool ok = true;
+                const bool writer = (tid >> 5) < writer_warps(nrows);
 #pragma unroll
-                    for (int c = 0; c < RT; ++c) rb[tid * RT + c] = acc[c];   // packed sums as they are
-                    if (RT == 1 && !D.out_f32) rb[tid] = acc[0] + acc1;
+                for (int q = 0; q < RT / RR; ++q) {
+                    if (q * RR >= r) break;
+                    double* rb = red + (size_t)(segphase % NRED) * kConsumers * RR;
+                    if (g < G) {
+#pragma unroll
+                        for (int c = 0; c < RR; ++c) rb[tid * RR + c] = acc[q * RR + c];   // packed sums as they are
+                        if (RT == 1 && !D.out_f32) rb[tid] = acc[0] + acc1;
+                    }
+                    mbar_arrive(segbar);
+                    if (!(ok = mbar_wait_or_abort(segbar, segphase++ & 1u, abortp))) break;
+                    if (writer) {
+                        const int cn = r - q * RR < RR ? r - q * RR : RR;
+                        write_segment(D, rb, RR, q * RR, cn, r, G, C.ws, C.ws32, C.u2, C.perm, C.N);
+                    }
+                    if (NRED == 1) {   // the single buffer is rewritten by the next round or segment
+                        mbar_arrive(segbar);
+                        if (!(ok = mbar_wait_or_abort(segbar, segphase++ & 1u, abortp))) break;
+                    }
                 }
-#pragma unroll
-                for (int c = 0; c < RT; ++c) acc[c] = 0.0;
-                acc1 = 0.0;
-                mbar_arrive(segbar);
-                if (!mbar_wait_or_abort(segbar, segphase++ & 1u, abortp)) {
+                if (!ok) {
                     atomicExch(a.err, 1);
                     abort_flag = 1;
                     break;
                 }
-                const bool writer = (tid >> 5) < writer_warps(nrows);
-                if (writer) write_segment<RT>(D, rb, r, G, C.ws, C.ws32, C.u2, C.perm, C.N);
-                if (NRED == 1) {   // the single buffer is rewritten by the next segment
-                    mbar_arrive(segbar);
-                    if (!mbar_wait_or_abort(segbar, segphase++ & 1u, abortp)) {
-                        atomicExch(a.err, 1);
-                        abort_flag = 1;
-                        break;
-                    }
-                }
+#pragma unroll
+                for (int c = 0; c < RT; ++c) acc[c] = 0.0;
+                acc1 = 0.0;
                 if (FLOW && writer && D.signal >= 0) {
                     __syncwarp();
                     if ((tid & 31) == 0) signal_region(a.cnt + D.signal);
@@ -1100,7 +1110,7 @@ static int tc_b_bytes(const h2_handle* op) {
 // `alo` + 2 `b` bytes.
 static size_t seg_smem_raw(int rt, int stages, int stage_bytes, int alo, int b, int sets) {
     const size_t S = (size_t)stages;
-    const size_t red = (size_t)red_buffers(rt) * sizeof(double) * kConsumers * rt;
+    const size_t red = (size_t)red_buffers(rt) * sizeof(double) * kConsumers * red_rhs(rt);
     const size_t tc = (size_t)sets * ((size_t)alo + 2 * (size_t)b);
     const size_t mid = red_buffers(rt) == 1 ? std::max(red, tc) : red + tc;
     return S * (size_t)stage_bytes + S * xin_bytes(rt) + mid + sizeof(uint64_t) * (2 * S + 5);
