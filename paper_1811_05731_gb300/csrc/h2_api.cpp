@@ -31,6 +31,11 @@ void free_device(h2_handle* h) {
         f(h->d_zero_rows); f(h->d_io); f(h->d_err);
         f(h->d_fseg); f(h->d_fchunk); f(h->d_fpiece); f(h->d_fdeps); f(h->d_fexpect); f(h->d_fzero_rows);
         f(h->d_fcnt);
+        f(h->d_sseg); f(h->d_schunk); f(h->d_spiece); f(h->d_sdeps); f(h->d_sexpect); f(h->d_szero_rows);
+        f(h->d_u2n);
+        if (h->near_stream) cudaStreamDestroy(h->near_stream);
+        if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+        if (h->ev_join) cudaEventDestroy(h->ev_join);
     }
 }
 
@@ -151,6 +156,7 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
         h2::FlowModel fm;
         rc = h2::flow_model(op, fm);
         if (rc == H2_OK) op->flow_makespan_us = h2::build_flow(op, fm);
+        if (rc == H2_OK && op->use_flow) rc = h2::build_split(op);
         if (p.schedule == H2_SCHEDULE_LEVELS) op->use_flow = 0;
     }
     if (rc == H2_OK) rc = h2::upload_plan(op);

@@ -258,6 +258,22 @@ struct h2_handle {
     int flow_grid = 0;                // CTAs of the last dataflow launch
     int nsm = 0;                      // SMs of the device
     int use_flow = 0;
+    // split form (reduced precision, r > 8, leaves of at most 64 rows): the
+    // FP64 near field in its own launch on a second stream (u2n), beside a
+    // dataflow launch of everything else (far field and leaf expansions, added
+    // into the cleared u2); one addition joins them
+    int has_split = 0;
+    int use_split = 1;                // autotuner's switch
+    h2::FlowOut split;                // ticket order without the near field
+    h2::FlowSeg* d_sseg = nullptr;
+    h2::Chunk* d_schunk = nullptr;
+    h2::Piece* d_spiece = nullptr;
+    int32_t* d_sdeps = nullptr;
+    int32_t* d_sexpect = nullptr;
+    int32_t* d_szero_rows = nullptr;
+    double* d_u2n = nullptr;          // max_rhs x N
+    cudaStream_t near_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // per-pass timing with CUDA events (profiling aid, off by default)
     int prof_enabled = 0;
     std::vector<std::vector<cudaEvent_t>> prof_calls;   // events of each profiled call
@@ -285,7 +301,10 @@ void build_block_partition(h2_handle* op);
 void gauss_legendre_unit(int q, std::vector<double>& x, std::vector<double>& w);
 void build_plan(h2_handle* op);   // arena layout + passes (h2_plan.cpp)
 double build_flow(h2_handle* op, const FlowModel& fm);   // dataflow order (h2_plan.cpp)
-double build_flow_multi(const std::vector<h2_handle*>& ops, const FlowModel& fm, FlowOut& out);
+double build_flow_multi(const std::vector<h2_handle*>& ops, const FlowModel& fm, FlowOut& out,
+                        bool without_near = false);
+bool split_possible(const h2_handle* op);   // the split form applies to this operator
+int build_split(h2_handle* op);             // its ticket order (host)
 
 // device-side assembly and matvec (h2_assemble.cu, h2_matvec.cu)
 int geometry_device_setup(h2_handle* g, cudaStream_t s);

@@ -953,6 +953,211 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Near field of the split form (r > 8, reduced-precision operators): the FP64
+// near blocks N_ts of every leaf t (Section "H2-Matrix Compression": the
+// inadmissible blocks, exact Lindholm entries, Psi on the diagonal of N_tt)
+// applied to all r right-hand sides and stored in `u2n` (r x N, mesh order).
+// It runs beside the far-field launch, which then has no FP64 work: the FP64
+// pipe and the tensor / FP32 pipes of an SM work at the same time.  One
+// producer warp stages each chunk as in k_seg (bulk copies of the matrices
+// and of their input rows); the eight consumer warps take the nrows x r
+// outputs of a segment as work items (row, right-hand side) dealt round-robin
+// to their 256 threads, every item over every column, so that no partial sums
+// meet across threads and the four SM sub-partitions get equal shares of the
+// FP64 work (two warps each, so that one's dependency waits are the other's
+// issue slots).  Segments are independent (no waits on other CTAs).
+// ---------------------------------------------------------------------------
+constexpr int kNearCons = 256;
+constexpr int kNearBlock = kNearCons + 32;
+
+struct NArgs {
+    const FlowSeg* seg;     // the near pass's segments (leaves, <= 64 rows)
+    const Chunk* chunk;
+    const Piece* piece;
+    int nseg;
+    const unsigned char* arena;
+    const double* ws;       // FP64 workspace: input rows in tree order
+    double* u2n;            // r x N
+    const int32_t* perm;
+    int64_t N;
+    int r;
+    int stages, stage_bytes;
+    int32_t* ticket;        // cleared by the gather
+    int32_t* err;
+};
+
+struct NStage {
+    int32_t seg, last, npieces, out_row, nrows;
+};
+
+// At most 40 registers per thread: one CTA of this kernel and one of the
+// far-field launch at r <= 16 (288 threads x 128 registers) share each SM
+// sub-partition's 16 K registers even where three warps of each meet.
+template <int RT>
+__global__ void __maxnreg__(40) k_near_items(const NArgs a) {
+    constexpr int JM = RT / 4;   // items per thread: 64 rows x RT / 256 threads
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int S = a.stages;
+    constexpr size_t kXin = xin_bytes(RT);
+    unsigned char* stage_base = smem;
+    unsigned char* xbase = smem + (size_t)S * a.stage_bytes;
+    uint64_t* full = reinterpret_cast<uint64_t*>(xbase + (size_t)S * kXin);
+    uint64_t* empty = full + S;
+    __shared__ NStage sd[kMaxStages];
+    __shared__ SPiece spc[kMaxStages][H2_MAX_CHUNK_PIECES];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int q = 0; q < S; ++q) {
+            mbar_init(&full[q], 2);
+            mbar_init(&empty[q], kNearCons);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    volatile int* abortp = &abort_flag;
+    int issued = 0;
+    const int r = a.r;
+    if (tid >= kNearCons) {
+        // ---------------- producer warp ----------------
+        const int lane = tid & 31;
+        int i = 0;
+        bool ok = true;
+        while (ok) {
+            int sg = 0;
+            if (lane == 0) sg = atomicAdd(a.ticket, 1);
+            sg = __shfl_sync(~0u, sg, 0);
+            const bool end = sg >= a.nseg;
+            const Segment F = end ? Segment{} : a.seg[sg].s;
+            for (int ci = 0; ci < (end ? 1 : F.nchunks); ++ci, ++i) {
+                const int st = i % S;
+                if (i >= S) {
+                    bool w = true;
+                    if (lane == 0) w = mbar_wait_or_abort(&empty[st], (uint32_t)((i / S) - 1) & 1u, abortp);
+                    if (!__shfl_sync(~0u, w, 0)) {
+                        if (lane == 0) {
+                            atomicExch(a.err, 1);
+                            abort_flag = 1;
+                        }
+                        ok = false;
+                        break;
+                    }
+                }
+                if (end) {   // end marker: complete the phase without a copy
+                    if (lane == 0) {
+                        sd[st].seg = -1;
+                        mbar_arrive(&full[st]);
+                        mbar_arrive(&full[st]);
+                    }
+                    ok = false;
+                    break;
+                }
+                const Chunk ch = a.chunk[F.chunk0 + ci];
+                if (lane == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    tma_load(stage_base + (size_t)st * a.stage_bytes, a.arena + ch.src, (uint32_t)ch.bytes, &full[st]);
+                }
+                ++issued;
+                Piece pc{};
+                if (lane < ch.npieces) pc = a.piece[ch.piece0 + lane];
+                const int mine = lane < ch.npieces ? input_bytes(pc.ncols, r, false) : 0;
+                int xoff = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(~0u, xoff, o);
+                    if (lane >= o) xoff += v;
+                }
+                const int in_total = __shfl_sync(~0u, xoff, 31);
+                xoff -= mine;
+                if (lane < ch.npieces) spc[st][lane] = SPiece{pc.smem_off, pc.in_row, pc.ncols, xoff};
+                if (lane == 0)
+                    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&full[st])),
+                                 "r"(in_total)
+                                 : "memory");
+                __syncwarp();
+                if (lane < ch.npieces) {
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_addr(xbase + (size_t)st * kXin + xoff)),
+                        "l"(a.ws + (int64_t)pc.in_row * r), "r"(mine), "r"(smem_addr(&full[st]))
+                        : "memory");
+                }
+                if (lane == 0) {
+                    sd[st] = NStage{sg, ci == F.nchunks - 1, ch.npieces, F.out_row, F.nrows};
+                    mbar_arrive(&full[st]);
+                }
+            }
+        }
+    } else {
+        // ---------------- consumer warps ----------------
+        double acc[JM];
+#pragma unroll
+        for (int j = 0; j < JM; ++j) acc[j] = 0.0;
+        int cur = -1, nitems = 0, nrows = 1;
+        int irow[JM], icol[JM];   // item j of this thread: output row, right-hand side
+        for (int i = 0;; ++i) {
+            const int st = i % S;
+            if (!mbar_wait_or_abort(&full[st], (uint32_t)(i / S) & 1u, abortp)) {
+                atomicExch(a.err, 1);
+                abort_flag = 1;
+                break;
+            }
+            const NStage D = sd[st];
+            if (D.seg < 0) break;
+            if (D.seg != cur) {   // items of a new segment
+                cur = D.seg;
+                nrows = D.nrows;
+                nitems = nrows * r;
+#pragma unroll
+                for (int j = 0; j < JM; ++j) {
+                    const int it = tid + kNearCons * j;
+                    irow[j] = it % nrows;
+                    icol[j] = it / nrows;
+                }
+            }
+            const unsigned char* stg = stage_base + (size_t)st * a.stage_bytes;
+            const unsigned char* xin = xbase + (size_t)st * kXin;
+            for (int p = 0; p < D.npieces; ++p) {
+                const SPiece P = spc[st][p];
+                const double* A = reinterpret_cast<const double*>(stg + P.smem_off);
+                const double* x = reinterpret_cast<const double*>(xin + P.xoff);
+#pragma unroll 2
+                for (int col = 0; col < P.ncols; ++col) {
+                    const double* Ac = A + col * nrows;
+                    const double* xc = x + col * r;
+#pragma unroll
+                    for (int j = 0; j < JM; ++j)
+                        if (tid + kNearCons * j < nitems) acc[j] = fma(Ac[irow[j]], xc[icol[j]], acc[j]);
+                }
+            }
+            mbar_arrive(&empty[st]);
+            if (D.last) {
+#pragma unroll
+                for (int j = 0; j < JM; ++j) {
+                    if (tid + kNearCons * j < nitems)
+                        a.u2n[(int64_t)icol[j] * a.N + a.perm[D.out_row + irow[j]]] = acc[j];
+                    acc[j] = 0.0;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // after an abort, let the producer's copies still in flight land (bounded)
+    if (tid == kNearCons && abort_flag) {
+        for (int j = issued > S ? issued - S : 0; j < issued; ++j)
+            (void)mbar_wait(&full[j % S], (uint32_t)(j / S) & 1u);
+    }
+}
+
+// u2 += u2n over n values (the split form's near field).
+__global__ void k_add(double* __restrict__ u2, const double* __restrict__ u2n, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        u2[i] += u2n[i];
+}
+
 // Gathers the input into the workspace's input rows (leaf by leaf in tree
 // order, padding rows zero) in FP64 and, for FP32 operators, in FP32; clears
 // the y-hat rows that are accumulated atomically (in the workspace of the
@@ -1140,11 +1345,123 @@ static int tc_sets_for(const h2_handle* op, int rt) {
     return tc_sets_raw(rt, op_stages(op, rt), op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op));
 }
 
+// ---- split form: shared memory of its two launches ----
+// near-field launch: two stages of matrices and FP64 inputs, 2 x 2 mbarriers
+static size_t near_smem_bytes(const h2_handle* op, int rt) {
+    return 2 * ((size_t)op->stage_bytes + xin_bytes(rt)) + 4 * sizeof(uint64_t);
+}
+// far-field launch: two stages, with two tensor-core operand sets when both
+// launches still fit one SM's shared memory (static parts and reserve aside)
+static int split_far_sets(const h2_handle* op, int rt) {
+    const size_t budget = (size_t)227 * 1024 - near_smem_bytes(op, rt) - (size_t)8 * 1024;
+    return seg_smem_raw(rt, 2, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op), 2) <= budget ? 2 : 1;
+}
+static size_t split_far_smem(const h2_handle* op, int rt) {
+    return seg_smem_raw(rt, 2, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op), split_far_sets(op, rt));
+}
+
+template <int RT>
+cudaError_t launch_near_rt(const NArgs& a, int nsm, size_t smem, cudaStream_t s) {
+    static size_t configured = 0;
+    cudaError_t e = set_smem(k_near_items<RT>, smem, configured);
+    if (e != cudaSuccess) return e;
+    k_near_items<RT><<<nsm, kNearBlock, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// The split form's launches after the gather: the near field on the
+// operator's second stream and the rest of the product on `s`, joined by an
+// addition (u2 += u2n).
+static int launch_split(h2_handle* op, double* u2, int r, int rt, cudaStream_t s, double* ws, float* ws32) {
+    const int64_t N = op->geom->N;
+    H2_CUDA_TRY(cudaMemsetAsync(u2, 0, sizeof(double) * (size_t)r * N, s));   // the expansions add into u2
+    H2_CUDA_TRY(cudaEventRecord(op->ev_fork, s));
+    H2_CUDA_TRY(cudaStreamWaitEvent(op->near_stream, op->ev_fork, 0));
+    const Pass* np = nullptr;
+    for (const Pass& p : op->passes)
+        if (p.kind == PASS_LEAF_NEAR) np = &p;
+    if (!np) return H2_ERR_INVALID_ARG;
+    NArgs na{};
+    na.seg = np->d_seg;
+    na.chunk = np->d_chunk;
+    na.piece = np->d_piece;
+    na.nseg = (int)np->seg.size();
+    na.arena = op->d_arena;
+    na.ws = ws;
+    na.u2n = op->d_u2n;
+    na.perm = op->d_perm;
+    na.N = N;
+    na.r = r;
+    na.stages = 2;
+    na.stage_bytes = op->stage_bytes;
+    na.ticket = op->d_fcnt + 3 * op->nc + 1;
+    na.err = op->d_err;
+    const size_t nsmem = near_smem_bytes(op, rt);
+    if (rt != 16) return H2_ERR_INVALID_ARG;   // split products have 9..16 right-hand sides
+    H2_CUDA_TRY(launch_near_rt<16>(na, op->nsm, nsmem, op->near_stream));
+    KArgs a{};
+    a.nops = 1;
+    a.ctx[0] = OpCtx{op->d_arena, ws, ws32, u2, op->d_perm, N, r, 0};
+    a.err = op->d_err;
+    a.r = r;
+    a.stages = 2;
+    a.stage_bytes = op->stage_bytes;
+    a.tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
+    a.tc_alo_bytes = tc_alo_bytes(op);
+    a.tc_b_bytes = tc_b_bytes(op);
+    a.tc_sets = split_far_sets(op, rt);
+    a.seg = op->d_sseg;
+    a.chunk = op->d_schunk;
+    a.piece = op->d_spiece;
+    a.deps = op->d_sdeps;
+    a.expect = op->d_sexpect;
+    a.cnt = op->d_fcnt;
+    a.nseg = (int)op->split.seg.size();
+    a.nreg = 3 * op->nc;
+    // one CTA per SM, so that a near-field CTA fits beside it
+    H2_CUDA_TRY(launch_seg<true>(a, rt, op->nsm, split_far_smem(op, rt), s, &op->flow_grid, 1));
+    H2_CUDA_TRY(cudaEventRecord(op->ev_join, op->near_stream));
+    H2_CUDA_TRY(cudaStreamWaitEvent(s, op->ev_join, 0));
+    const int64_t n = (int64_t)r * N;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4 * (int64_t)op->nsm));
+    k_add<<<grid, 256, 0, s>>>(u2, op->d_u2n, n);
+    H2_CUDA_TRY(cudaGetLastError());
+    return H2_OK;
+}
+
+static bool split_active(const h2_handle* op, bool flow, int rt) {
+    return flow && op->has_split && op->use_split && rt > 8;
+}
+
+// Kernel launches of one product with max_rhs right-hand sides.
+static int launches_per_matvec(const h2_handle* op) {
+    if (!op->use_flow) return 1 + (int)op->passes.size();
+    const int r = op->params.max_rhs;
+    if (!split_active(op, true, rt_for(r))) return 2;
+    // products of at most 16 right-hand sides: 4 launches each (a rest of at
+    // most 8 is one single-launch product: 2)
+    const int rest = r % 16;
+    return 4 * (r / 16) + (rest == 0 ? 0 : rest > 8 ? 4 : 2);
+}
+
 // Launches the gather kernel and every pass (level-wise) or the flow kernel
 // on workspaces `ws` (FP64) and `ws32` (FP32 operators only).
 int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream_t s, double* ws,
                   float* ws32, bool flow, std::vector<cudaEvent_t>* marks,
                   std::vector<cudaEvent_t>* pool) {
+    if (r > 16 && split_active(op, flow, rt_for(r))) {
+        // the split form in products of at most 16 right-hand sides: at 32 a
+        // far-field CTA (168 registers per thread) leaves no SM sub-partition
+        // room for a near-field warp, at 16 both fit
+        // (profiling marks: the first product's gather, then all the rest)
+        for (int c0 = 0; c0 < r; c0 += 16) {
+            const int rc = launch_matvec(op, u1 + (int64_t)c0 * op->geom->N, u2 + (int64_t)c0 * op->geom->N,
+                                         std::min(16, r - c0), s, ws, ws32, flow, c0 == 0 ? marks : nullptr, pool);
+            if (rc != H2_OK) return rc;
+        }
+        if (marks && !marks->empty()) H2_CUDA_TRY(cudaEventRecord(marks->back(), s));
+        return H2_OK;
+    }
     const int rt = rt_for(r);
     if ((int64_t)op->chunk_cols * r > (int64_t)xin_cols(rt) * rt) return H2_ERR_INVALID_ARG;   // stage inputs
     const size_t smem = pass_smem_bytes(op, rt);
@@ -1163,10 +1480,11 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
         return cudaEventRecord(e, s);
     };
     H2_CUDA_TRY(mark());
+    const bool split = split_active(op, flow, rt);
     {
-        const std::vector<int32_t>& zr = flow ? op->fzero_rows : op->zero_rows;
-        const int32_t* d_zr = flow ? op->d_fzero_rows : op->d_zero_rows;
-        const int nclear = flow ? 3 * op->nc + 1 : 0;
+        const std::vector<int32_t>& zr = split ? op->split.zero_rows[0] : flow ? op->fzero_rows : op->zero_rows;
+        const int32_t* d_zr = split ? op->d_szero_rows : flow ? op->d_fzero_rows : op->d_zero_rows;
+        const int nclear = flow ? 3 * op->nc + 2 : 0;
         const int64_t work = std::max<int64_t>({op->row_xhat * r, (int64_t)zr.size() * op->kp * r, (int64_t)nclear});
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 4096));
         k_prologue<<<grid, 256, 0, s>>>(u1, ws, ws32, op->d_gather_src, op->row_xhat, N, r, d_zr, (int)zr.size(),
@@ -1174,6 +1492,12 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
         H2_CUDA_TRY(cudaGetLastError());
     }
     H2_CUDA_TRY(mark());
+    if (split) {
+        const int rc = launch_split(op, u2, r, rt, s, ws, ws32);
+        if (rc != H2_OK) return rc;
+        H2_CUDA_TRY(mark());
+        return H2_OK;
+    }
     KArgs a{};
     a.nops = 1;
     a.ctx[0] = OpCtx{op->d_arena, ws, ws32, u2, op->d_perm, N, r, 0};
@@ -1245,6 +1569,35 @@ int flow_model(h2_handle* op, FlowModel& fm) {
     return flow_model_raw(rt, tc, pass_smem_bytes(op, rt), op->params.max_rhs, fm, op->tune_ctas);
 }
 
+// The split form applies to FP32 and BF16 hi+lo operators built for more than
+// 8 right-hand sides whose leaves have at most 64 rows (the near-field
+// kernel's work items: 64 rows x r over 128 threads, r / 2 per thread).
+bool split_possible(const h2_handle* op) {
+    const int p = op->params.precision;
+    if ((p != H2_FP32 && p != H2_BF16X3) || op->params.max_rhs <= 8) return false;
+    bool near = false;
+    for (const Pass& q : op->passes)
+        if (q.kind == PASS_LEAF_NEAR) {
+            near = true;
+            for (const Segment& sg : q.seg)
+                if (sg.nrows > 64) return false;
+        }
+    return near;
+}
+
+int build_split(h2_handle* op) {
+    op->has_split = 0;
+    if (!split_possible(op)) return H2_OK;
+    const int rt = rt_for(op->params.max_rhs);
+    const bool tc = op->params.precision == H2_BF16X3;
+    FlowModel fm;
+    const int rc = flow_model_raw(rt, tc, split_far_smem(op, rt), op->params.max_rhs, fm, 1);
+    if (rc != H2_OK) return rc;
+    if (build_flow_multi({op}, fm, op->split, true) < 0.0) return H2_OK;   // single launch only
+    op->has_split = 1;
+    return H2_OK;
+}
+
 // Checks, on the host, the invariants the bulk copies rely on (16-byte aligned
 // sources, destinations and sizes; chunks within one stage; input rows on
 // 4-row boundaries), so that a plan that violates them is rejected before any
@@ -1298,7 +1651,7 @@ static int upload_flow(h2_handle* op) {
         (rc = upload_vec(op->fpiece, &op->d_fpiece)) || (rc = upload_vec(op->fdeps, &op->d_fdeps)) ||
         (rc = upload_vec(op->fexpect, &op->d_fexpect)) || (rc = upload_vec(op->fzero_rows, &op->d_fzero_rows)))
         return rc;
-    if (!op->d_fcnt) H2_CUDA_TRY(cudaMalloc((void**)&op->d_fcnt, sizeof(int32_t) * (3 * (size_t)op->nc + 1)));
+    if (!op->d_fcnt) H2_CUDA_TRY(cudaMalloc((void**)&op->d_fcnt, sizeof(int32_t) * (3 * (size_t)op->nc + 2)));
     return H2_OK;
 }
 
@@ -1328,13 +1681,29 @@ int upload_plan(h2_handle* op) {
     op->nsm = nsm;
     if ((rc = upload_vec(op->zero_rows, &op->d_zero_rows))) return rc;
     if (op->use_flow && (rc = upload_flow(op))) return rc;
+    if (op->has_split) {
+        if (validate_chunks(op, nullptr, op->split.chunk, op->split.piece) != H2_OK) {
+            set_last_error("h2_assemble: internal plan check failed (split dataflow chunks)");
+            return H2_ERR_INVALID_ARG;
+        }
+        if ((rc = upload_vec(op->split.seg, &op->d_sseg)) || (rc = upload_vec(op->split.chunk, &op->d_schunk)) ||
+            (rc = upload_vec(op->split.piece, &op->d_spiece)) || (rc = upload_vec(op->split.deps, &op->d_sdeps)) ||
+            (rc = upload_vec(op->split.expect, &op->d_sexpect)) ||
+            (rc = upload_vec(op->split.zero_rows[0], &op->d_szero_rows)))
+            return rc;
+        if (!op->d_fcnt) H2_CUDA_TRY(cudaMalloc((void**)&op->d_fcnt, sizeof(int32_t) * (3 * (size_t)op->nc + 2)));
+        H2_CUDA_TRY(cudaMalloc((void**)&op->d_u2n, sizeof(double) * (size_t)op->params.max_rhs * op->geom->N));
+        H2_CUDA_TRY(cudaStreamCreateWithFlags(&op->near_stream, cudaStreamNonBlocking));
+        H2_CUDA_TRY(cudaEventCreateWithFlags(&op->ev_fork, cudaEventDisableTiming));
+        H2_CUDA_TRY(cudaEventCreateWithFlags(&op->ev_join, cudaEventDisableTiming));
+    }
     if ((rc = upload_vec(op->gather_src, &op->d_gather_src))) return rc;
     H2_CUDA_TRY(cudaMalloc((void**)&op->d_ws, sizeof(double) * (size_t)op->ws_rows * op->params.max_rhs));
     if (op->params.precision != H2_FP64)
         H2_CUDA_TRY(cudaMalloc((void**)&op->d_ws32, sizeof(float) * (size_t)op->ws_rows * op->params.max_rhs));
     H2_CUDA_TRY(cudaMalloc((void**)&op->d_err, sizeof(int)));
     H2_CUDA_TRY(cudaMemset(op->d_err, 0, sizeof(int)));
-    op->n_launches = op->use_flow ? 2 : 1 + (int)op->passes.size();
+    op->n_launches = launches_per_matvec(op);
     return H2_OK;
 }
 
@@ -1478,8 +1847,10 @@ int autotune(h2_handle* op, int r, cudaStream_t s, h2_tuning_t* out) {
     const int iters = std::max(1, std::min(10, (int)(20.0 / std::max(ms0, 1e-3))));
     if (rc == H2_OK) rc = time_products(op, x, y, r, s, iters, &ms0);
     int best_flow = use_flow0, best_st = st0, best_ct = ct0, ncand = 0;
-    double best = ms0;
     const int rt = rt_for(r);
+    const bool can_split = op->has_split && rt > 8;
+    int best_split = op->use_split;
+    double best = ms0;
     const bool tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
     for (int flow = have_flow ? 1 : 0; flow >= 0 && rc == H2_OK; --flow) {
         for (int stages = 2; stages <= 4 && rc == H2_OK; ++stages) {
@@ -1498,6 +1869,7 @@ int autotune(h2_handle* op, int r, cudaStream_t s, h2_tuning_t* out) {
             for (int cap = 1; cap <= std::min(occ, 4) && rc == H2_OK; ++cap) {
                 op->tune_ctas = cap;
                 op->use_flow = flow;
+                op->use_split = 0;
                 if (flow && (rc = rebuild_flow(op)) != H2_OK) break;
                 double ms = 0.0;
                 rc = time_products(op, x, y, r, s, iters, &ms);
@@ -1507,17 +1879,31 @@ int autotune(h2_handle* op, int r, cudaStream_t s, h2_tuning_t* out) {
                     best_flow = flow;
                     best_st = stages;
                     best_ct = cap;
+                    best_split = 0;
                 }
             }
         }
     }
+    if (can_split && rc == H2_OK) {   // the split form (its own stage and CTA counts)
+        op->use_flow = 1;
+        op->use_split = 1;
+        double ms = 0.0;
+        rc = time_products(op, x, y, r, s, iters, &ms);
+        ++ncand;
+        if (rc == H2_OK && ms < best) {
+            best = ms;
+            best_flow = 1;
+            best_split = 1;
+        }
+    }
+    op->use_split = best_split;
     op->use_flow = best_flow;
     op->tune_stages = best_st;
     op->tune_ctas = best_ct;
     op->tune_ms = best;
     if (rc == H2_OK && have_flow) rc = rebuild_flow(op);   // the order for the chosen CTA count
     op->use_flow = best_flow;
-    op->n_launches = op->use_flow ? 2 : 1 + (int)op->passes.size();
+    op->n_launches = launches_per_matvec(op);
     cudaFree(x);
     cudaFree(y);
     if (out) {

@@ -360,7 +360,10 @@ void build_plan(h2_handle* op) {
 // multiply-adds and matrix bytes at one CTA's share of the SM and HBM rates.
 // Returns the simulated makespan in microseconds (or -1 if the dataflow form
 // could not be built; the level-wise launches are used then).
-double build_flow_multi(const std::vector<h2_handle*>& ops, const FlowModel& fm, FlowOut& out) {
+// without_near: the near-field segments are left out (the split form runs
+// them in a launch of their own) and the leaf expansions add into u2 without
+// waiting for them.
+double build_flow_multi(const std::vector<h2_handle*>& ops, const FlowModel& fm, FlowOut& out, bool without_near) {
     out = FlowOut{};
     struct Item {
         FlowSeg fs;
@@ -389,6 +392,7 @@ double build_flow_multi(const std::vector<h2_handle*>& ops, const FlowModel& fm,
         std::vector<char> zero(2 * nc, 0);   // x-hat (c) and y-hat (nc + c) regions written atomically
         producers.resize((size_t)reg_base + 3 * nc, 0);
         for (const Pass& p : op->passes) {
+            if (without_near && p.kind == PASS_LEAF_NEAR) continue;
             for (const Segment& sg0 : p.seg) {
                 Item it{};
                 it.fs.s = sg0;
@@ -422,7 +426,7 @@ double build_flow_multi(const std::vector<h2_handle*>& ops, const FlowModel& fm,
                     if (sg0.mode == SEG_FINAL) it.fs.signal = reg_base + 2 * nc + c;
                     else {
                         it.fs.signal = -1;
-                        it.deps.push_back(reg_base + 2 * nc + c);   // after the near field of the leaf
+                        if (!without_near) it.deps.push_back(reg_base + 2 * nc + c);   // after the near field of the leaf
                     }
                 } else {
                     int rb;

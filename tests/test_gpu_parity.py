@@ -240,3 +240,26 @@ def test_graph_replay_and_autotune():
     op2 = pkg.Operator(g, m=4, leaf=64, max_rhs=2, precision=pkg.BF16X3, autotune=True)
     y2 = op2.matvec(xd).cpu().numpy()
     assert np.all(rel_err(y2, ref) <= REDUCED_TOL["bf16x3"])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_split_form_runs_and_matches_oracle(precision):
+    """Reduced-precision operators for more than 8 right-hand sides run the near
+    field in its own launch beside the far-field dataflow launch, in products of
+    at most 16 right-hand sides (gather, near field, far field, join: 4
+    launches; a rest of at most 8 is one single-launch product: 2).  The
+    product still meets the budget against the oracle for r at and below the
+    operator's maximum: 24 = 16 + 8, 17 = 16 + 1, 9 (one split product), 3
+    (no split)."""
+    m = synth.cube_sphere(9)
+    g = pkg.Geometry(m.xyz, m.tri)
+    op = pkg.Operator(g, m=4, leaf=20, max_rhs=24, precision=PRECISIONS[precision])
+    assert op.stats()["n_launches_matvec"] == 4 + 2
+    o = oracle.H2Oracle(m.xyz, m.tri, 4, 20, 2.0)
+    for r in (24, 17, 9, 3):
+        x = _inputs(m, r, seed=11)
+        ref = o.matvec(x)
+        y = op.matvec(torch.from_numpy(x).cuda(), nan_out(torch.from_numpy(x).cuda())).cpu().numpy()
+        assert pkg.h2_device_status(op.handle) == 0
+        err = np.max(np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1))
+        assert err <= REDUCED_TOL[precision], (r, err)
