@@ -1350,14 +1350,23 @@ static int tc_sets_for(const h2_handle* op, int rt) {
 static size_t near_smem_bytes(const h2_handle* op, int rt) {
     return 2 * ((size_t)op->stage_bytes + xin_bytes(rt)) + 4 * sizeof(uint64_t);
 }
-// far-field launch: two stages, with two tensor-core operand sets when both
-// launches still fit one SM's shared memory (static parts and reserve aside)
-static int split_far_sets(const h2_handle* op, int rt) {
+// far-field launch: three stages with one tensor-core operand set when both
+// launches still fit one SM's shared memory (static parts and reserve aside),
+// else two stages with two sets or one (measured: the third stage in flight
+// is worth more than the second set)
+struct FarCfg {
+    int stages, sets;
+};
+static FarCfg split_far_cfg(const h2_handle* op, int rt) {
     const size_t budget = (size_t)227 * 1024 - near_smem_bytes(op, rt) - (size_t)8 * 1024;
-    return seg_smem_raw(rt, 2, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op), 2) <= budget ? 2 : 1;
+    const int alo = tc_alo_bytes(op), b = tc_b_bytes(op);
+    if (seg_smem_raw(rt, 3, op->stage_bytes, alo, b, 1) <= budget) return FarCfg{3, 1};
+    if (seg_smem_raw(rt, 2, op->stage_bytes, alo, b, 2) <= budget) return FarCfg{2, 2};
+    return FarCfg{2, 1};
 }
 static size_t split_far_smem(const h2_handle* op, int rt) {
-    return seg_smem_raw(rt, 2, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op), split_far_sets(op, rt));
+    const FarCfg c = split_far_cfg(op, rt);
+    return seg_smem_raw(rt, c.stages, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op), c.sets);
 }
 
 template <int RT>
@@ -1404,12 +1413,13 @@ static int launch_split(h2_handle* op, double* u2, int r, int rt, cudaStream_t s
     a.ctx[0] = OpCtx{op->d_arena, ws, ws32, u2, op->d_perm, N, r, 0};
     a.err = op->d_err;
     a.r = r;
-    a.stages = 2;
+    const FarCfg fc = split_far_cfg(op, rt);
+    a.stages = fc.stages;
     a.stage_bytes = op->stage_bytes;
     a.tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
     a.tc_alo_bytes = tc_alo_bytes(op);
     a.tc_b_bytes = tc_b_bytes(op);
-    a.tc_sets = split_far_sets(op, rt);
+    a.tc_sets = fc.sets;
     a.seg = op->d_sseg;
     a.chunk = op->d_schunk;
     a.piece = op->d_spiece;
