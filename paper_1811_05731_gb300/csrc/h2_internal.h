@@ -54,9 +54,9 @@ inline __host__ __device__ int tc_rows(int nrows) { return nrows <= 64 ? 64 : 12
 // Columns (the MMA's K) multiplied by one tcgen05.mma.
 inline __host__ __device__ int tc_kstep(int type) { return type == PIECE_TF32 ? 8 : 16; }
 // Consumer warps that write a finished segment (and, in the dataflow form,
-// each signal its region once): one per 32 rows on the CUDA cores; the four
+// each signal its region once): one per 16 rows on the CUDA cores; the four
 // warps that own the TMEM lane quarters for tensor-core segments.
-inline __host__ __device__ int segment_writers(int nrows, bool tc) { return tc ? 4 : (nrows + 31) / 32; }
+inline __host__ __device__ int segment_writers(int nrows, bool tc) { return tc ? 4 : (nrows + 15) / 16; }
 // Byte offset of entry (i, j) in a tensor-core tile of Mp rows.  The tile is a
 // sequence of K slabs (tc_kstep columns each, all rows); a slab holds two
 // "core matrices" along K, each Mp/8 groups of 8 rows x 16 bytes, so that

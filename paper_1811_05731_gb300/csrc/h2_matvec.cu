@@ -357,21 +357,28 @@ __device__ __forceinline__ float packed_sum(const double* red, int stride, int G
 }
 
 // Writer warps of a segment: warp w < writer_warps(nrows) adds the G partial
-// sums of rows 32w .. 32w+31 (one row per lane) for right-hand sides c0 ..
-// c0+cn-1, stored in `red` with stride `rs` per thread, and writes them; the
-// other consumer warps go on with the next chunk.
-__host__ __device__ constexpr int writer_warps(int nrows) { return (nrows + 31) / 32; }
+// sums of rows 16w .. 16w+15 (lanes l and l+16: row 16w + l, the first and the
+// second half of the right-hand sides c0 .. c0+cn-1), stored in `red` with
+// stride `rs` per thread, and writes them; up to all eight consumer warps share
+// the writing, the others go on with the next chunk.  One right-hand side
+// (cn == 1 always): rows 32w .. 32w+31, one per lane, and the writer warps
+// past the rows only signal.
+__host__ __device__ constexpr int writer_warps(int nrows) { return (nrows + 15) / 16; }
 
 __device__ __forceinline__ void write_segment(const StageDesc& D, const double* red, int rs, int c0, int cn, int r,
                                               int G, double* ws, float* ws32, double* u2,
                                               const int32_t* __restrict__ perm, int64_t N) {
     const int nrows = D.nrows;
-    const int rr = threadIdx.x;   // writer warps only: threadIdx.x < 32 * writer_warps(nrows)
+    const int lane = threadIdx.x & 31;
+    const bool one = rs == 1;
+    const int rr = one ? (int)threadIdx.x : 16 * (threadIdx.x >> 5) + (lane & 15);   // writer warps only
     if (rr >= nrows) return;
+    const int ch = (cn + 1) >> 1;
+    const int cb = one || lane < 16 ? 0 : ch, ce = one ? cn : lane < 16 ? ch : cn;
     const bool fin = D.mode == SEG_FINAL || D.mode == SEG_FINAL_ADD;
     const int64_t orow = fin ? (int64_t)perm[D.out_row + rr] : (int64_t)(D.out_row + rr) * r;
     if (D.out_f32) {   // packed FP32 partial sums, FP32 output
-        for (int c = 0; c < cn; ++c) {
+        for (int c = cb; c < ce; ++c) {
             const float v = packed_sum(red + rr * rs + c, nrows * rs, G);
             float* dst = ws32 + orow + c0 + c;
             if (D.mode == SEG_STORE) *dst = v;
@@ -380,13 +387,14 @@ __device__ __forceinline__ void write_segment(const StageDesc& D, const double* 
         }
         return;
     }
-    for (int c = 0; c < cn; ++c) {
+    for (int c = cb; c < ce; ++c) {
         double s = 0.0;
         for (int g2 = 0; g2 < G; ++g2) s += red[(g2 * nrows + rr) * rs + c];
         double* dst = fin ? u2 + (int64_t)(c0 + c) * N + orow : ws + orow + c0 + c;
         if (D.mode == SEG_STORE || D.mode == SEG_FINAL) *dst = s;
-        else if (D.mode == SEG_ADD || D.mode == SEG_FINAL_ADD) *dst = __ldcg(dst) + s;
-        else atomicAdd(dst, s);
+        else if (D.mode == SEG_ADD) *dst = __ldcg(dst) + s;
+        else atomicAdd(dst, s);   // SEG_ATOMIC; SEG_FINAL_ADD too (its value's only adder: the
+                                  // same sum as a read-modify-write, without the load's latency)
     }
 }
 
@@ -453,10 +461,12 @@ __host__ __device__ constexpr size_t xin_bytes(int rt) {
 
 // Partial-sum buffers of the segment kernel: two (alternating between
 // segments, so one barrier per segment suffices) while they are small.
-__host__ __device__ constexpr int red_buffers(int rt) { return rt <= 8 ? 2 : 1; }
-// Right-hand sides per reduction round: all of them up to 8, else rounds of 8
-// (two consumer barriers per round), which keeps the buffer at 16 KB.
-__host__ __device__ constexpr int red_rhs(int rt) { return rt <= 8 ? rt : 8; }
+__host__ __device__ constexpr int red_buffers(int rt) { return 2; }
+// Right-hand sides per reduction round: all of them up to 8, else rounds of 4,
+// which keeps the two buffers at 16 KB.  Rounds alternate between the
+// buffers, so one consumer barrier per round suffices and nobody waits for
+// the writers' global stores.
+__host__ __device__ constexpr int red_rhs(int rt) { return rt <= 8 ? rt : 4; }
 
 // Shared-memory layout of the segment kernel (dynamic part):
 //   stages x stage_bytes             matrix chunks (bulk copies)
