@@ -225,7 +225,7 @@ struct h2_handle {
     double assemble_seconds = 0.0;
     int stages = 3;                   // shared-memory stages of the pass kernel
     int stage_bytes = 32768;
-    int coupling_split = 4;           // far blocks per coupling segment
+    int coupling_split = 8;           // far blocks per coupling segment
     int chunk_cols = H2_MAX_CHUNK_COLS;   // input columns per chunk (chunk_cols_for(max_rhs))
     double flow_makespan_us = 0.0;    // simulated duration of the dataflow order
     // CUDA graph of one matvec (the gather and the product launches), captured
