@@ -53,10 +53,11 @@ inline __host__ __device__ bool piece_tc(int type) { return type >= PIECE_TF32; 
 inline __host__ __device__ int tc_rows(int nrows) { return nrows <= 64 ? 64 : 128; }
 // Columns (the MMA's K) multiplied by one tcgen05.mma.
 inline __host__ __device__ int tc_kstep(int type) { return type == PIECE_TF32 ? 8 : 16; }
-// Consumer warps that write a finished segment (and, in the dataflow form,
-// each signal its region once): one per 16 rows on the CUDA cores; the four
-// warps that own the TMEM lane quarters for tensor-core segments.
-inline __host__ __device__ int segment_writers(int nrows, bool tc) { return tc ? 4 : (nrows + 15) / 16; }
+// Signal units of a finished segment in the dataflow form: one per 16 rows
+// (the CUDA-core writer warps each write and signal 16 rows; of a tensor-core
+// segment, the four warps that own the TMEM lane quarters signal one unit per
+// 16-row group they wrote), whichever pipe multiplied it.
+inline __host__ __device__ int segment_writers(int nrows, bool tc) { return (void)tc, (nrows + 15) / 16; }
 // Byte offset of entry (i, j) in a tensor-core tile of Mp rows.  The tile is a
 // sequence of K slabs (tc_kstep columns each, all rows); a slab holds two
 // "core matrices" along K, each Mp/8 groups of 8 rows x 16 bytes, so that
@@ -226,6 +227,7 @@ struct h2_handle {
     int stages = 3;                   // shared-memory stages of the pass kernel
     int stage_bytes = 32768;
     int coupling_split = 8;           // far blocks per coupling segment
+    int tc_small_r_cuda = 1;          // tensor-core tiles on the CUDA cores at small r (autotuner's switch)
     int chunk_cols = H2_MAX_CHUNK_COLS;   // input columns per chunk (chunk_cols_for(max_rhs))
     double flow_makespan_us = 0.0;    // simulated duration of the dataflow order
     // CUDA graph of one matvec (the gather and the product launches), captured

@@ -149,6 +149,7 @@ struct KArgs {
     int tc_nacc;               // accumulators of the hi*hi products (K steps round-robin)
     int tc_ncorr;              // accumulators of the correction products (round-robin)
     int tc_np;                 // accumulator width: right-hand sides rounded up to 16
+    int tc_cuda;               // 1: tensor-core tiles multiplied on the CUDA cores (small r)
     int nops;                  // operators of the launch (several: a batched product)
     OpCtx ctx[H2_MAX_BATCH];
 };
@@ -167,8 +168,8 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parit
         if (*abort_flag || now_ns() - t0 > kWaitNs) return false;
     }
 }
-__device__ __forceinline__ void signal_region(int32_t* p) {
-    asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(p) : "memory");
+__device__ __forceinline__ void signal_region(int32_t* p, int n = 1) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(n) : "memory");
 }
 
 // The producer warp's source of segments (lane 0).  FLOW: the global ticket
@@ -339,6 +340,76 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const 
     } else {
 #pragma unroll
         for (int c = 0; c < RT; ++c) acc[c] += (double)acc32[c];
+    }
+}
+
+// Largest r at which tensor-core tiles may be multiplied on the CUDA cores.
+constexpr int kTcCudaMaxRT = 4;
+
+// Tensor-core tiles (3xTF32, BF16 hi + lo) multiplied on the CUDA cores, for
+// few right-hand sides, where one tcgen05.mma of N = 8..16 columns costs as much
+// as one of 128 and the products are bound by the bytes streamed: the same
+// stored values (TF32 tiles: FP32 entries; BF16: hi + lo, exact in FP32),
+// FP32 FMAs, the chunk's sums added to the packed compensated FP32 pair (the
+// segments of these tiles have FP32 outputs).  Thread (row, g) takes the
+// 16-byte core rows g, g+G, ... of its row (4 TF32 or 8 BF16 columns each,
+// see tc_offset), so that a warp reads 512 contiguous bytes per core row.
+template <int RT>
+__device__ __forceinline__ void consume_tc_tiles(const unsigned char* stage, const SPiece* pieces, int npieces,
+                                                 int type, const unsigned char* xin, int r, int nrows, int row,
+                                                 int g, int G, double (&acc)[RT]) {
+    const int Mp = tc_rows(nrows);
+    const int ks = tc_kstep(type);
+    const bool bf = type == PIECE_BF16X3;
+    const int per = bf ? 8 : 4;
+    const int64_t slab = (int64_t)ks * Mp * 4;
+    const int rowoff = (row >> 3) * 128 + (row & 7) * 16;
+    float acc32[RT];
+#pragma unroll
+    for (int c = 0; c < RT; ++c) acc32[c] = 0.0f;
+    for (int p = 0; p < npieces; ++p) {
+        const SPiece P = pieces[p];
+        const unsigned char* T = stage + P.smem_off + rowoff;
+        const float* x = reinterpret_cast<const float*>(xin + P.xoff);
+        const int units = 2 * ((P.ncols + ks - 1) / ks);   // core rows of this row: two per K slab
+        for (int u = g; u < units; u += G) {
+            const int j0 = (u >> 1) * ks + (u & 1) * per;
+            if (j0 >= P.ncols) continue;
+            const unsigned char* src = T + (u >> 1) * slab + (u & 1) * 16 * Mp;
+            float a[8];
+            if (bf) {
+                const uint4 h = *reinterpret_cast<const uint4*>(src);
+                const uint4 l = *reinterpret_cast<const uint4*>(src + 32 * Mp);
+                const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {   // bf16 -> f32: the 16 bits as the high half
+                    a[2 * e] = __uint_as_float(hw[e] << 16) + __uint_as_float(lw[e] << 16);
+                    a[2 * e + 1] = __uint_as_float(hw[e] & 0xFFFF0000u) + __uint_as_float(lw[e] & 0xFFFF0000u);
+                }
+            } else {
+                const float4 v = *reinterpret_cast<const float4*>(src);
+                a[0] = v.x;
+                a[1] = v.y;
+                a[2] = v.z;
+                a[3] = v.w;
+            }
+            const int ne = P.ncols - j0 < per ? P.ncols - j0 : per;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                if (e >= per || e >= ne) break;
+                const float* xj = x + (j0 + e) * r;
+#pragma unroll
+                for (int c = 0; c < RT; ++c)
+                    if (c < r) acc32[c] = fmaf(a[e], xj[c], acc32[c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < RT; ++c) {
+        float s, e;
+        two_sum(__int_as_float(__double2hiint(acc[c])), acc32[c], s, e);
+        const float l = __int_as_float(__double2loint(acc[c])) + e;
+        acc[c] = __hiloint2double(__float_as_int(s), __float_as_int(l));
     }
 }
 
@@ -699,7 +770,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
             if (D.seg < 0) break;
             const OpCtx& C = a.ctx[D.op];
             const int r = C.r;
-            if (TC && piece_tc(D.ptype)) {
+            if (TC && piece_tc(D.ptype) && !a.tc_cuda) {
                 // ---------- tensor-core chunk ----------
                 unsigned char* stg = stage_base + (size_t)st * a.stage_bytes;
                 const unsigned char* xin = xbase + (size_t)st * kXin;
@@ -885,9 +956,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                             }
                         }
                         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                        if (FLOW && D.signal >= 0) {
+                        if (FLOW && D.signal >= 0) {   // one unit per 16-row group of the segment it wrote
+                            const int ng = Mp == 128 ? (32 * w < D.nrows) + (32 * w + 16 < D.nrows) : (16 * w < D.nrows);
                             __syncwarp();
-                            if (lane == 0) signal_region(a.cnt + D.signal);
+                            if (lane == 0 && ng > 0) signal_region(a.cnt + D.signal, ng);
                         }
                     }
                     segk = 0;
@@ -904,9 +976,19 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
             const int nrows = D.nrows;
             const int G = kConsumers / nrows;
             const int row = tid % nrows, g = tid / nrows;
-            if (g < G)
-                consume_chunk<RT>(stage_base + (size_t)st * a.stage_bytes, spc[st], D.npieces, D.f32 != 0,
-                                  xbase + (size_t)st * kXin, r, nrows, row, g, G, D.out_f32 != 0, acc, acc1);
+            if (g < G) {
+                bool done = false;
+                if constexpr (!TC && RT <= kTcCudaMaxRT) {   // tensor tiles on the CUDA cores (a.tc_cuda)
+                    if (piece_tc(D.ptype)) {
+                        consume_tc_tiles<RT>(stage_base + (size_t)st * a.stage_bytes, spc[st], D.npieces, D.ptype,
+                                             xbase + (size_t)st * kXin, r, nrows, row, g, G, acc);
+                        done = true;
+                    }
+                }
+                if (!done)
+                    consume_chunk<RT>(stage_base + (size_t)st * a.stage_bytes, spc[st], D.npieces, D.f32 != 0,
+                                      xbase + (size_t)st * kXin, r, nrows, row, g, G, D.out_f32 != 0, acc, acc1);
+            }
             mbar_arrive(&empty[st]);
             if (D.last) {
                 // partial sums of the row groups, RR right-hand sides per round
@@ -1351,7 +1433,14 @@ static int tc_sets_raw(int rt, int stages, int stage_bytes, int alo, int b) {
 static size_t seg_smem_bytes(const h2_handle* op, int rt, int sets) {
     return seg_smem_raw(rt, op_stages(op, rt), op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op), sets);
 }
+// Tensor-core tiles multiplied on the CUDA cores: at most kTcCudaMaxRT
+// right-hand sides (the autotuner may turn it off).
+static bool tc_cuda_for(const h2_handle* op, int rt) {
+    const int p = op->params.precision;
+    return (p == H2_TF32X3 || p == H2_BF16X3) && rt <= kTcCudaMaxRT && op->tc_small_r_cuda;
+}
 static int tc_sets_for(const h2_handle* op, int rt) {
+    if (tc_cuda_for(op, rt)) return 0;   // no tensor-core operands
     return tc_sets_raw(rt, op_stages(op, rt), op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op));
 }
 
@@ -1525,10 +1614,11 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
     a.r = r;
     a.stages = op_stages(op, rt);
     a.stage_bytes = op->stage_bytes;
-    a.tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
+    a.tc = (op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3) && !tc_cuda_for(op, rt);
     a.tc_alo_bytes = tc_alo_bytes(op);
     a.tc_b_bytes = tc_b_bytes(op);
     a.tc_sets = tc_sets_for(op, rt);
+    a.tc_cuda = tc_cuda_for(op, rt) ? 1 : 0;
     if (flow) {
         a.seg = op->d_fseg;
         a.chunk = op->d_fchunk;
@@ -1585,7 +1675,7 @@ static int flow_model_raw(int rt, bool tc, size_t smem, int r, FlowModel& fm, in
 
 int flow_model(h2_handle* op, FlowModel& fm) {
     const int rt = rt_for(op->params.max_rhs);
-    const bool tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
+    const bool tc = (op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3) && !tc_cuda_for(op, rt);
     return flow_model_raw(rt, tc, pass_smem_bytes(op, rt), op->params.max_rhs, fm, op->tune_ctas);
 }
 
@@ -1871,7 +1961,7 @@ int autotune(h2_handle* op, int r, cudaStream_t s, h2_tuning_t* out) {
     const bool can_split = op->has_split && rt > 8;
     int best_split = op->use_split;
     double best = ms0;
-    const bool tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
+    const bool tc = (op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3) && !tc_cuda_for(op, rt);
     for (int flow = have_flow ? 1 : 0; flow >= 0 && rc == H2_OK; --flow) {
         for (int stages = 2; stages <= 4 && rc == H2_OK; ++stages) {
             op->tune_stages = stages;
@@ -1917,6 +2007,20 @@ int autotune(h2_handle* op, int r, cudaStream_t s, h2_tuning_t* out) {
         }
     }
     op->use_split = best_split;
+    // tensor-core tiles on the CUDA cores or on the tensor cores (small r)
+    const int prec = op->params.precision;
+    if (rc == H2_OK && (prec == H2_TF32X3 || prec == H2_BF16X3) && rt <= kTcCudaMaxRT) {
+        const int cur = op->tc_small_r_cuda;
+        op->use_flow = best_flow;
+        op->tune_stages = best_st;
+        op->tune_ctas = best_ct;
+        op->tc_small_r_cuda = !cur;
+        double ms = 0.0;
+        rc = time_products(op, x, y, r, s, iters, &ms);
+        ++ncand;
+        if (rc == H2_OK && ms < best) best = ms;
+        else op->tc_small_r_cuda = cur;
+    }
     op->use_flow = best_flow;
     op->tune_stages = best_st;
     op->tune_ctas = best_ct;
@@ -1991,7 +2095,8 @@ int matvec_batched(h2_handle* const* ops, int n, const double* const* u1, double
     const int rt = rt_for(rmax);
     const int stage_bytes = ops[0]->stage_bytes;
     const int nst = stages_for(rt, stage_bytes, alo, b);
-    const int sets = tc ? tc_sets_raw(rt, nst, stage_bytes, alo, b) : 1;
+    const bool tcc = tc && rt <= kTcCudaMaxRT;   // tensor tiles on the CUDA cores
+    const int sets = tcc ? 0 : tc ? tc_sets_raw(rt, nst, stage_bytes, alo, b) : 1;
     const size_t smem = seg_smem_raw(rt, nst, stage_bytes, alo, b, sets);
     for (int i = 0; i < n; ++i)   // a stage holds every chunk's inputs
         if ((int64_t)ops[i]->chunk_cols * r[i] > (int64_t)xin_cols(rt) * rt) return H2_ERR_INVALID_ARG;
@@ -2048,10 +2153,11 @@ int matvec_batched(h2_handle* const* ops, int n, const double* const* u1, double
     a.r = rmax;
     a.stages = nst;
     a.stage_bytes = stage_bytes;
-    a.tc = tc;
+    a.tc = tc && !tcc;
     a.tc_alo_bytes = alo;
     a.tc_b_bytes = b;
     a.tc_sets = sets;
+    a.tc_cuda = tcc ? 1 : 0;
     a.seg = bp->d_seg;
     a.chunk = bp->d_chunk;
     a.piece = bp->d_piece;

@@ -43,8 +43,14 @@ def test_batched_small_meshes_match_oracle_and_single_products():
             y = y.cpu().numpy()
             tol = 1e-8 if prec == pkg.FP64 else (1e-4 if prec == pkg.BF16X3 else 1e-5)
             assert np.all(rel_err(y, ref) <= tol), (prec, rel_err(y, ref))
-            # same segments, same arithmetic; only the order of atomic additions differs
-            assert np.all(rel_err(y, single) <= (1e-13 if prec == pkg.FP64 else 1e-6)), (prec, rel_err(y, single))
+            # same segments and arithmetic, only the order of atomic additions
+            # differs -- except for tensor-core tiles, which the batched launch
+            # (r up to 5: the tensor cores) and the single product of r <= 4 (the
+            # CUDA cores) multiply on different pipes: both within the budget
+            if prec in (pkg.TF32X3, pkg.BF16X3) and r <= 4:
+                assert np.all(rel_err(y, single) <= tol), (prec, rel_err(y, single))
+            else:
+                assert np.all(rel_err(y, single) <= (1e-13 if prec == pkg.FP64 else 1e-6)), (prec, rel_err(y, single))
 
 
 def test_batched_eight_uneven_meshes():
