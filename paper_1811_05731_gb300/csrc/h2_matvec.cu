@@ -530,9 +530,9 @@ __host__ __device__ constexpr size_t xin_bytes(int rt) {
     return sizeof(double) * xin_cols(rt) * rt + 16 * H2_MAX_CHUNK_PIECES;
 }
 
-// Partial-sum buffers of the segment kernel: two (alternating between
-// segments, so one barrier per segment suffices) while they are small.
-__host__ __device__ constexpr int red_buffers(int rt) { return 2; }
+// Partial-sum buffers of the segment kernel: two, alternating between the
+// reduction rounds of successive segments.
+constexpr int kRedBuffers = 2;
 // Right-hand sides per reduction round: all of them up to 8, else rounds of 4,
 // which keeps the two buffers at 16 KB.  Rounds alternate between the
 // buffers, so one consumer barrier per round suffices and nobody waits for
@@ -542,9 +542,10 @@ __host__ __device__ constexpr int red_rhs(int rt) { return rt <= 8 ? rt : 4; }
 // Shared-memory layout of the segment kernel (dynamic part):
 //   stages x stage_bytes             matrix chunks (bulk copies)
 //   stages x xin_bytes(RT)           the chunks' input values
-//   red_buffers x kConsumers*red_rhs(RT)*8   partial sums of the row groups
-//   tc_alo_bytes, 2 x tc_b_bytes     tensor-core operands (TF32 lo parts, B hi / lo)
-//   stages x 2 + 3 mbarriers         full[], empty[], segment, operands-ready, products-done
+//   2 x kConsumers*red_rhs(RT)*8     partial sums of the row groups (two buffers)
+//   tc_sets x (tc_alo_bytes + 2 x tc_b_bytes)   tensor-core operands (TF32 lo parts of A,
+//                                    B with its hi rows and its lo rows)
+//   stages x 2 + 5 mbarriers         full[], empty[], segment, operands-ready[2], products-done[2]
 //
 // Warp specialisation.  The producer warp (the last warp) walks this CTA's
 // chunks: it waits until the consumers released the stage, issues the bulk
@@ -555,32 +556,26 @@ __host__ __device__ constexpr int red_rhs(int rt) { return rt <= 8 ? rt : 4; }
 // on the stage's `full` barrier, which completes when the bulk copy has
 // landed.  The 8 consumer warps wait on `full`, multiply, release the stage
 // on `empty` and, at the end of a segment, add the row groups' partial sums
-// (one mbarrier-based barrier among the consumers); the writer warps write
-// the segment and, in the dataflow form, each signals the segment's region
-// with a release add.  No CTA-wide barrier is taken per chunk and no
-// wait is unbounded.
+// (one mbarrier-based barrier among the consumers per reduction round); the
+// writer warps write the segment and, in the dataflow form, each signals the
+// segment's region with a release add.  No CTA-wide barrier is taken per
+// chunk and no wait is unbounded.
 template <int RT, bool FLOW, bool TC>
 __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int S = a.stages;
     constexpr size_t kXin = xin_bytes(RT);
-    constexpr int NRED = red_buffers(RT);
     constexpr int RR = red_rhs(RT);
     unsigned char* stage_base = smem;
     unsigned char* xbase = smem + (size_t)S * a.stage_bytes;
     double* red = reinterpret_cast<double*>(xbase + (size_t)S * kXin);
-    // tensor-core operands: after the partial sums, or over them when there is
-    // a single partial-sum buffer (its readers finish behind a consumer barrier
-    // before the next chunk is prepared)
-    // operand set q: [lo parts of A][B hi][B lo] at tc_base + q * tc_set_bytes
-    unsigned char* tc_base = NRED == 1 ? reinterpret_cast<unsigned char*>(red)
-                                       : reinterpret_cast<unsigned char*>(red + NRED * kConsumers * RR);
+    // tensor-core operands after the partial sums;
+    // operand set q: [lo parts of A][B: hi rows, lo rows] at tc_base + q * tc_set_bytes
+    unsigned char* tc_base = reinterpret_cast<unsigned char*>(red + kRedBuffers * kConsumers * RR);
     const size_t tc_set_bytes = (size_t)a.tc_alo_bytes + 2 * (size_t)a.tc_b_bytes;
-    const size_t red_span = (size_t)NRED * kConsumers * RR * sizeof(double);
+    const size_t red_span = (size_t)kRedBuffers * kConsumers * RR * sizeof(double);
     const size_t tc_span = (size_t)a.tc_sets * tc_set_bytes;
-    uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(red) +
-                                                  (NRED == 1 ? (red_span > tc_span ? red_span : tc_span)
-                                                             : red_span + tc_span));
+    uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(red) + red_span + tc_span);
     uint64_t* empty = full + S;
     uint64_t* segbar = empty + S;
     uint64_t* cbar = segbar + 1;     // [2]: tensor operands of chunk n ready (barrier n & 1)
@@ -997,7 +992,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
 #pragma unroll
                 for (int q = 0; q < RT / RR; ++q) {
                     if (q * RR >= r) break;
-                    double* rb = red + (size_t)(segphase % NRED) * kConsumers * RR;
+                    double* rb = red + (size_t)(segphase % kRedBuffers) * kConsumers * RR;
                     if (g < G) {
 #pragma unroll
                         for (int c = 0; c < RR; ++c) rb[tid * RR + c] = acc[q * RR + c];   // packed sums as they are
@@ -1008,10 +1003,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                     if (writer) {
                         const int cn = r - q * RR < RR ? r - q * RR : RR;
                         write_segment(D, rb, RR, q * RR, cn, r, G, C.ws, C.ws32, C.u2, C.perm, C.N);
-                    }
-                    if (NRED == 1) {   // the single buffer is rewritten by the next round or segment
-                        mbar_arrive(segbar);
-                        if (!(ok = mbar_wait_or_abort(segbar, segphase++ & 1u, abortp))) break;
                     }
                 }
                 if (!ok) {
@@ -1407,9 +1398,9 @@ static int tc_b_bytes(const h2_handle* op) {
 // `alo` + 2 `b` bytes.
 static size_t seg_smem_raw(int rt, int stages, int stage_bytes, int alo, int b, int sets) {
     const size_t S = (size_t)stages;
-    const size_t red = (size_t)red_buffers(rt) * sizeof(double) * kConsumers * red_rhs(rt);
+    const size_t red = (size_t)kRedBuffers * sizeof(double) * kConsumers * red_rhs(rt);
     const size_t tc = (size_t)sets * ((size_t)alo + 2 * (size_t)b);
-    const size_t mid = red_buffers(rt) == 1 ? std::max(red, tc) : red + tc;
+    const size_t mid = red + tc;
     return S * (size_t)stage_bytes + S * xin_bytes(rt) + mid + sizeof(uint64_t) * (2 * S + 5);
 }
 
