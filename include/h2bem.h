@@ -67,7 +67,12 @@ typedef enum {
  *             (hi = bf16(a), lo = bf16(a - hi), 4 bytes per entry) and
  *             multiplied on the tensor cores as hi*hi + hi*lo + lo*hi with the
  *             vectors split the same way, FP32 accumulation.  Leaf bases FP32.
- * The reduced forms target a relative error <= 1e-5 against the FP64 form. */
+ * For products of at most 4 right-hand sides the H2_TF32X3 and H2_BF16X3 tiles
+ * are multiplied on the CUDA cores (the same stored values, FP32 products and
+ * accumulation), where one tensor-core instruction of so few columns costs as
+ * much as one of 128; h2_autotune may choose the tensor cores instead.
+ * The reduced forms target a relative error <= 1e-5 against the FP64 form
+ * (BF16 hi + lo keeps about 17 significant bits of each entry). */
 typedef enum { H2_FP64 = 0, H2_FP32 = 1, H2_TF32X3 = 2, H2_BF16X3 = 3 } h2_precision;
 
 typedef struct {
@@ -169,10 +174,14 @@ typedef struct {
  * and products of r right-hand sides on zero-filled scratch vectors, every
  * combination of the schedule (the single dataflow launch or one launch per
  * pass), 2..4 shared-memory stages and 1..max resident CTAs per SM that fits,
- * keeps the fastest for later h2_matvec calls (the dataflow ticket order is
- * rebuilt for its CTA count) and reports it in *out (may be NULL).  The
- * matrices, their layout and the results do not change.  Allocates and frees
- * its scratch vectors; synchronous.  1 <= r <= max_rhs. */
+ * and, where they apply, the split form (r > 8, FP32 and BF16 hi+lo: the FP64
+ * near field in its own launch beside the rest) and the pipe of 3xTF32 / BF16
+ * hi+lo tiles at r <= 4 (CUDA cores or tensor cores); keeps the fastest for
+ * later h2_matvec calls (the dataflow ticket order is rebuilt for its CTA
+ * count) and reports it in *out (may be NULL; `schedule` reports the split
+ * form as H2_SCHEDULE_FLOW).  The matrices and their layout do not change; the
+ * results change only by rounding.  Allocates and frees its scratch vectors;
+ * synchronous.  1 <= r <= max_rhs. */
 int h2_autotune(h2_handle* op, int32_t r, void* cuda_stream, h2_tuning_t* out);
 
 /* Counts and sizes of an operator (Section "Results", "Data compression":
