@@ -32,7 +32,7 @@ void free_device(h2_handle* h) {
         f(h->d_fseg); f(h->d_fchunk); f(h->d_fpiece); f(h->d_fdeps); f(h->d_fexpect); f(h->d_fzero_rows);
         f(h->d_fcnt);
         f(h->d_sseg); f(h->d_schunk); f(h->d_spiece); f(h->d_sdeps); f(h->d_sexpect); f(h->d_szero_rows);
-        f(h->d_u2n);
+        f(h->d_u2n); f(h->d_near_units);
         if (h->near_stream) cudaStreamDestroy(h->near_stream);
         if (h->ev_fork) cudaEventDestroy(h->ev_fork);
         if (h->ev_join) cudaEventDestroy(h->ev_join);

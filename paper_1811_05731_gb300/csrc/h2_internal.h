@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <string>
 #include <vector>
 
@@ -274,6 +275,8 @@ struct h2_handle {
     int32_t* d_sexpect = nullptr;
     int32_t* d_szero_rows = nullptr;
     double* d_u2n = nullptr;          // max_rhs x N
+    std::vector<std::array<int32_t, 4>> near_units;   // near-field work units: segment, first chunk, chunks
+    int4* d_near_units = nullptr;
     cudaStream_t near_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // per-pass timing with CUDA events (profiling aid, off by default)

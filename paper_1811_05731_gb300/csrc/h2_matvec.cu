@@ -1049,7 +1049,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
 // to their 256 threads, every item over every column, so that no partial sums
 // meet across threads and the four SM sub-partitions get equal shares of the
 // FP64 work (two warps each, so that one's dependency waits are the other's
-// issue slots).  Segments are independent (no waits on other CTAs).
+// issue slots).  The CTAs take work units from an atomic ticket, longest
+// first: a segment, or a run of its chunks where a few SMs would otherwise
+// finish the largest leaves alone; a unit's sums are added to the cleared
+// u2n (a value receives one addition per unit of its leaf).  No unit waits
+// for another.
 // ---------------------------------------------------------------------------
 constexpr int kNearCons = 256;
 constexpr int kNearBlock = kNearCons + 32;
@@ -1058,7 +1062,8 @@ struct NArgs {
     const FlowSeg* seg;     // the near pass's segments (leaves, <= 64 rows)
     const Chunk* chunk;
     const Piece* piece;
-    int nseg;
+    const int4* units;      // work units: segment, first chunk in it, chunks
+    int nunits;
     const unsigned char* arena;
     const double* ws;       // FP64 workspace: input rows in tree order
     double* u2n;            // r x N
@@ -1109,12 +1114,13 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
         int i = 0;
         bool ok = true;
         while (ok) {
-            int sg = 0;
-            if (lane == 0) sg = atomicAdd(a.ticket, 1);
-            sg = __shfl_sync(~0u, sg, 0);
-            const bool end = sg >= a.nseg;
-            const Segment F = end ? Segment{} : a.seg[sg].s;
-            for (int ci = 0; ci < (end ? 1 : F.nchunks); ++ci, ++i) {
+            int un = 0;
+            if (lane == 0) un = atomicAdd(a.ticket, 1);
+            un = __shfl_sync(~0u, un, 0);
+            const bool end = un >= a.nunits;
+            const int4 U = end ? make_int4(0, 0, 1, 0) : a.units[un];
+            const Segment F = end ? Segment{} : a.seg[U.x].s;
+            for (int ci = 0; ci < U.z; ++ci, ++i) {
                 const int st = i % S;
                 if (i >= S) {
                     bool w = true;
@@ -1137,7 +1143,7 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
                     ok = false;
                     break;
                 }
-                const Chunk ch = a.chunk[F.chunk0 + ci];
+                const Chunk ch = a.chunk[F.chunk0 + U.y + ci];
                 if (lane == 0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     tma_load(stage_base + (size_t)st * a.stage_bytes, a.arena + ch.src, (uint32_t)ch.bytes, &full[st]);
@@ -1169,7 +1175,7 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
                         : "memory");
                 }
                 if (lane == 0) {
-                    sd[st] = NStage{sg, ci == F.nchunks - 1, ch.npieces, F.out_row, F.nrows};
+                    sd[st] = NStage{un, ci == U.z - 1, ch.npieces, F.out_row, F.nrows};
                     mbar_arrive(&full[st]);
                 }
             }
@@ -1190,7 +1196,7 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
             }
             const NStage D = sd[st];
             if (D.seg < 0) break;
-            if (D.seg != cur) {   // items of a new segment
+            if (D.seg != cur) {   // items of a new work unit
                 cur = D.seg;
                 nrows = D.nrows;
                 nitems = nrows * r;
@@ -1221,7 +1227,7 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
 #pragma unroll
                 for (int j = 0; j < JM; ++j) {
                     if (tid + kNearCons * j < nitems)
-                        a.u2n[(int64_t)icol[j] * a.N + a.perm[D.out_row + irow[j]]] = acc[j];
+                        atomicAdd(a.u2n + (int64_t)icol[j] * a.N + a.perm[D.out_row + irow[j]], acc[j]);
                     acc[j] = 0.0;
                 }
             }
@@ -1474,6 +1480,7 @@ cudaError_t launch_near_rt(const NArgs& a, int nsm, size_t smem, cudaStream_t s)
 static int launch_split(h2_handle* op, double* u2, int r, int rt, cudaStream_t s, double* ws, float* ws32) {
     const int64_t N = op->geom->N;
     H2_CUDA_TRY(cudaMemsetAsync(u2, 0, sizeof(double) * (size_t)r * N, s));   // the expansions add into u2
+    H2_CUDA_TRY(cudaMemsetAsync(op->d_u2n, 0, sizeof(double) * (size_t)r * N, s));   // the near-field units too
     H2_CUDA_TRY(cudaEventRecord(op->ev_fork, s));
     H2_CUDA_TRY(cudaStreamWaitEvent(op->near_stream, op->ev_fork, 0));
     const Pass* np = nullptr;
@@ -1484,7 +1491,8 @@ static int launch_split(h2_handle* op, double* u2, int r, int rt, cudaStream_t s
     na.seg = np->d_seg;
     na.chunk = np->d_chunk;
     na.piece = np->d_piece;
-    na.nseg = (int)np->seg.size();
+    na.units = op->d_near_units;
+    na.nunits = (int)op->near_units.size();
     na.arena = op->d_arena;
     na.ws = ws;
     na.u2n = op->d_u2n;
@@ -1695,6 +1703,25 @@ int build_split(h2_handle* op) {
     const int rc = flow_model_raw(rt, tc, split_far_smem(op, rt), op->params.max_rhs, fm, 1);
     if (rc != H2_OK) return rc;
     if (build_flow_multi({op}, fm, op->split, true) < 0.0) return H2_OK;   // single launch only
+    // near-field work units: runs of at most `maxc` chunks of a segment, so
+    // that there are about 8 units per SM; longest first
+    const Pass* np = nullptr;
+    for (const Pass& p : op->passes)
+        if (p.kind == PASS_LEAF_NEAR) np = &p;
+    int64_t total = 0;
+    for (const Segment& sg : np->seg) total += sg.nchunks;
+    const int maxc = (int)std::max<int64_t>(2, (total + 8LL * fm.workers - 1) / (8LL * fm.workers));
+    op->near_units.clear();
+    for (size_t i = 0; i < np->seg.size(); ++i) {
+        const int nch = np->seg[i].nchunks;
+        const int parts = (nch + maxc - 1) / maxc;
+        for (int q = 0; q < parts; ++q) {
+            const int c0 = (int)((int64_t)nch * q / parts), c1 = (int)((int64_t)nch * (q + 1) / parts);
+            op->near_units.push_back({(int32_t)i, c0, c1 - c0, 0});
+        }
+    }
+    std::stable_sort(op->near_units.begin(), op->near_units.end(),
+                     [](const std::array<int32_t, 4>& x, const std::array<int32_t, 4>& y) { return x[2] > y[2]; });
     op->has_split = 1;
     return H2_OK;
 }
@@ -1794,6 +1821,9 @@ int upload_plan(h2_handle* op) {
             return rc;
         if (!op->d_fcnt) H2_CUDA_TRY(cudaMalloc((void**)&op->d_fcnt, sizeof(int32_t) * (3 * (size_t)op->nc + 2)));
         H2_CUDA_TRY(cudaMalloc((void**)&op->d_u2n, sizeof(double) * (size_t)op->params.max_rhs * op->geom->N));
+        H2_CUDA_TRY(cudaMalloc((void**)&op->d_near_units, sizeof(int4) * std::max<size_t>(1, op->near_units.size())));
+        H2_CUDA_TRY(cudaMemcpy(op->d_near_units, op->near_units.data(), sizeof(int4) * op->near_units.size(),
+                               cudaMemcpyHostToDevice));
         H2_CUDA_TRY(cudaStreamCreateWithFlags(&op->near_stream, cudaStreamNonBlocking));
         H2_CUDA_TRY(cudaEventCreateWithFlags(&op->ev_fork, cudaEventDisableTiming));
         H2_CUDA_TRY(cudaEventCreateWithFlags(&op->ev_join, cudaEventDisableTiming));

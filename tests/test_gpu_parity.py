@@ -263,3 +263,22 @@ def test_split_form_runs_and_matches_oracle(precision):
         assert pkg.h2_device_status(op.handle) == 0
         err = np.max(np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1))
         assert err <= REDUCED_TOL[precision], (r, err)
+
+
+def test_autotuner_with_split_and_tile_pipe_candidates():
+    """The autotuner's extra candidates (the split form above 8 right-hand sides;
+    the CUDA-core / tensor-core pipe for 3xTF32 tiles at r <= 4) keep the product
+    within the budget against the oracle, whichever it picks."""
+    m = synth.cube_sphere(9)
+    g = pkg.Geometry(m.xyz, m.tri)
+    o = oracle.H2Oracle(m.xyz, m.tri, 4, 20, 2.0)
+    for precision, r in (("fp32", 12), ("tf32x3", 3)):
+        op = pkg.Operator(g, m=4, leaf=20, max_rhs=r, precision=PRECISIONS[precision], autotune=True)
+        x = _inputs(m, r, seed=13)
+        ref = o.matvec(x)
+        xt = torch.from_numpy(x).cuda()
+        for _ in range(3):   # direct launch, graph capture, graph replay
+            y = op.matvec(xt, nan_out(xt)).cpu().numpy()
+            assert pkg.h2_device_status(op.handle) == 0
+            err = np.max(np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1))
+            assert err <= REDUCED_TOL[precision], (precision, r, err)
