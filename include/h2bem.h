@@ -120,7 +120,11 @@ int h2_assemble(const h2_handle* geom, const h2_params* p, h2_handle** out_op);
  *           order of the input mesh.  Either both device pointers or both
  *           host pointers; with host pointers the call copies in and out on
  *           `cuda_stream` and returns after the result is in u2.
- *   1 <= r <= max_rhs.  u1 and u2 must not overlap.  u2 is overwritten. */
+ *   1 <= r <= max_rhs.  u1 and u2 must not overlap.  u2 is overwritten.
+ * The work is ordered on `cuda_stream`; FP32 and BF16 hi+lo operators with
+ * r > 8 also run the near field on a stream of the operator, joined to
+ * `cuda_stream` by events before the call's last launch (the result is
+ * complete when `cuda_stream` reaches that point, as for every call). */
 int h2_matvec(h2_handle* op, const double* u1, double* u2, int32_t r, void* cuda_stream);
 
 /* u2_i = M_i u1_i for several operators at once (several meshes, e.g. of
