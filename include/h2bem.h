@@ -84,8 +84,20 @@ typedef struct {
     int32_t max_rhs;        /* largest r accepted by h2_matvec (workspace size), >= 1 */
     int32_t schedule;       /* h2_schedule: how one h2_matvec is launched              */
     int32_t autotune;       /* 1: h2_assemble ends with h2_autotune(op, max_rhs)       */
-    int32_t reserved[2];    /* must be zero                                           */
+    int32_t coupling;       /* h2_coupling: stored S_ts (default) or evaluated        */
+    int32_t reserved[1];    /* must be zero                                           */
 } h2_params;
+
+/* H2_COUPLING_STORED (default): the coupling matrices S_ts are assembled and
+ *   stored in the operator's precision and streamed by every product.
+ * H2_COUPLING_ON_THE_FLY (H2_FP32 operators only): every product evaluates
+ *   S_ts(nu, mu) = 1 / (4 pi |x^t_nu - x^s_mu|) (Section "H2-Matrix
+ *   Compression": the coupling matrices are the kernel at the interpolation
+ *   nodes) in FP32 from the Chebyshev nodes, stored per block relative to the
+ *   target box's centre so that the difference keeps its digits; the coupling
+ *   matrices, the largest part of the far field, are neither stored nor
+ *   streamed. */
+typedef enum { H2_COUPLING_STORED = 0, H2_COUPLING_ON_THE_FLY = 1 } h2_coupling;
 
 /* H2_SCHEDULE_FLOW (default): one persistent kernel after the input gather;
  *   its CTAs take the product's segments in a dependency order and wait

@@ -329,6 +329,51 @@ __global__ void k_coupling(const CouplingItem* __restrict__ items, int m,
     }
 }
 
+// Coupling blocks evaluated in the product (H2_COUPLING_ON_THE_FLY): per block,
+// the source cluster's Chebyshev nodes minus the target box's centre, one
+// float4 per column (the difference in FP64, rounded once).
+__global__ void k_coupling_nodes(const CouplingItem* __restrict__ items, int m, const double* __restrict__ box,
+                                 unsigned char* arena) {
+    const CouplingItem it = items[blockIdx.x];
+    const int k = m * m * m;
+    __shared__ double off[3], h[3], cosv[H2_MAX_M];
+    if (threadIdx.x == 0) {
+        for (int d = 0; d < 3; ++d) {
+            const double* bs = box + 6 * (int64_t)it.s;
+            const double* bt = box + 6 * (int64_t)it.t;
+            off[d] = 0.5 * (bs[d] + bs[3 + d]) - 0.5 * (bt[d] + bt[3 + d]);   // source centre - target centre
+            h[d] = 0.5 * (bs[3 + d] - bs[d]);
+        }
+        for (int j = 0; j < m; ++j) cosv[j] = cos((2.0 * j + 1.0) * kPi / (2.0 * m));
+    }
+    __syncthreads();
+    float4* dst = reinterpret_cast<float4*>(arena + it.off);
+    for (int mu = threadIdx.x; mu < k; mu += blockDim.x) {
+        const int a = mu / (m * m), b = (mu / m) % m, c = mu % m;
+        dst[mu] = make_float4((float)(off[0] + h[0] * cosv[a]), (float)(off[1] + h[1] * cosv[b]),
+                              (float)(off[2] + h[2] * cosv[c]), 0.0f);
+    }
+}
+
+// Every cluster's Chebyshev nodes minus its box's centre (kp float4 per
+// cluster): the target side of the evaluated coupling blocks.
+__global__ void k_cluster_nodes(int m, int kp, const double* __restrict__ box, float4* __restrict__ out) {
+    const int cl = blockIdx.x;
+    const int k = m * m * m;
+    const double* b = box + 6 * (int64_t)cl;
+    for (int nu = threadIdx.x; nu < kp; nu += blockDim.x) {
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (nu < k) {
+            const int ia[3] = {nu / (m * m), (nu / m) % m, nu % m};
+            float w[3];
+            for (int d = 0; d < 3; ++d)
+                w[d] = (float)(0.5 * (b[3 + d] - b[d]) * cos((2.0 * ia[d] + 1.0) * kPi / (2.0 * m)));
+            v = make_float4(w[0], w[1], w[2], 0.0f);
+        }
+        out[(int64_t)cl * kp + nu] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Lindholm's closed form for a linear basis on a flat triangle.  For the
 // triangle T = (r0, r1, r2) with unit normal n ~ (r1 - r0) x (r2 - r0), area A,
@@ -568,7 +613,13 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
     CouplingItem* d_ci = nullptr;
     if ((rc = upload(ci, &d_ci, s))) { cleanup(); return rc; }
     tmp.push_back(d_ci);
-    if (!ci.empty()) k_coupling<<<(unsigned)ci.size(), 256, 0, s>>>(d_ci, m, op->d_box, op->d_arena, tt);
+    if (op->params.coupling == H2_COUPLING_ON_THE_FLY) {   // nodes only: the product evaluates S_ts
+        if (!op->d_nodes) H2_CUDA_TRY(cudaMalloc((void**)&op->d_nodes, sizeof(float4) * (size_t)op->nc * op->kp));
+        k_cluster_nodes<<<(unsigned)op->nc, 128, 0, s>>>(m, op->kp, op->d_box, op->d_nodes);
+        if (!ci.empty()) k_coupling_nodes<<<(unsigned)ci.size(), 128, 0, s>>>(d_ci, m, op->d_box, op->d_arena);
+    } else if (!ci.empty()) {
+        k_coupling<<<(unsigned)ci.size(), 256, 0, s>>>(d_ci, m, op->d_box, op->d_arena, tt);
+    }
 
     std::vector<NearItem> ni(op->near_t.size());
     int maxleaf = 1;

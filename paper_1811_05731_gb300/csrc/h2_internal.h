@@ -47,9 +47,13 @@ enum SegMode : int32_t {
 // How a stored matrix is laid out and multiplied.  PIECE_F64 / PIECE_F32:
 // column-major, CUDA cores.  PIECE_TF32 / PIECE_BF16X3: a tensor-core tile
 // (see tc_offset), multiplied by tcgen05.
-enum PieceType : int32_t { PIECE_F64 = 0, PIECE_F32 = 1, PIECE_TF32 = 2, PIECE_BF16X3 = 3 };
+enum PieceType : int32_t { PIECE_F64 = 0, PIECE_F32 = 1, PIECE_TF32 = 2, PIECE_BF16X3 = 3, PIECE_NODES = 4 };
+// PIECE_NODES: a coupling block evaluated in the product (H2_COUPLING_ON_THE_FLY):
+// one float4 per column, the source cluster's Chebyshev node minus the target
+// box's centre; the target nodes (minus the same centre) come from the
+// operator's per-cluster node table.
 
-inline __host__ __device__ bool piece_tc(int type) { return type >= PIECE_TF32; }
+inline __host__ __device__ bool piece_tc(int type) { return type == PIECE_TF32 || type == PIECE_BF16X3; }
 // Rows of a tensor-core tile (the MMA's M) for a block of `nrows` rows.
 inline __host__ __device__ int tc_rows(int nrows) { return nrows <= 64 ? 64 : 128; }
 // Columns (the MMA's K) multiplied by one tcgen05.mma.
@@ -277,6 +281,7 @@ struct h2_handle {
     double* d_u2n = nullptr;          // max_rhs x N
     std::vector<std::array<int32_t, 4>> near_units;   // near-field work units: segment, first chunk, chunks
     int4* d_near_units = nullptr;
+    float4* d_nodes = nullptr;        // evaluated coupling: kp Chebyshev nodes per cluster, minus its box's centre
     cudaStream_t near_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // per-pass timing with CUDA events (profiling aid, off by default)

@@ -125,7 +125,9 @@ struct OpCtx {
     const int32_t* perm;
     int64_t N;
     int r;
-    int pad;
+    int kp;                    // cluster vector rows (evaluated coupling: the node table's stride)
+    const float4* nodes;       // evaluated coupling: Chebyshev nodes minus the box centre, per cluster
+    int64_t row_yhat;          // first y-hat row of the workspace
 };
 
 struct KArgs {
@@ -340,6 +342,55 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const 
     } else {
 #pragma unroll
         for (int c = 0; c < RT; ++c) acc[c] += (double)acc32[c];
+    }
+}
+
+// Coupling blocks evaluated in the product (H2_COUPLING_ON_THE_FLY): each
+// staged column is a source node y (minus the target box's centre), the
+// thread's row a target node x (minus the same centre), and the block entry
+// S(x, y) = 1 / (4 pi |x - y|) is formed in FP32 (rsqrtf) and applied to the
+// column's inputs; sums as for FP32 chunks (packed compensated pair).
+constexpr float kInv4Pi = 0.0795774715459476679f;
+
+template <int RT>
+__device__ __forceinline__ void consume_nodes(const unsigned char* stage, const SPiece* pieces, int npieces,
+                                              const unsigned char* xin, int r, float4 xt, int g, int G,
+                                              double (&acc)[RT]) {
+    float acc32[RT];
+#pragma unroll
+    for (int c = 0; c < RT; ++c) acc32[c] = 0.0f;
+    for (int p = 0; p < npieces; ++p) {
+        const SPiece P = pieces[p];
+        const float4* Y = reinterpret_cast<const float4*>(stage + P.smem_off);
+        const float* x = reinterpret_cast<const float*>(xin + P.xoff);
+#pragma unroll 2
+        for (int col = g; col < P.ncols; col += G) {
+            const float4 y = Y[col];
+            const float dx = xt.x - y.x, dy = xt.y - y.y, dz = xt.z - y.z;
+            const float sv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * kInv4Pi;
+            if (RT % 4 == 0 && r == RT) {
+                const float4* x4 = reinterpret_cast<const float4*>(x + col * RT);
+#pragma unroll
+                for (int c = 0; c < RT / 4; ++c) {
+                    const float4 xv = x4[c];
+                    acc32[4 * c] = fmaf(sv, xv.x, acc32[4 * c]);
+                    acc32[4 * c + 1] = fmaf(sv, xv.y, acc32[4 * c + 1]);
+                    acc32[4 * c + 2] = fmaf(sv, xv.z, acc32[4 * c + 2]);
+                    acc32[4 * c + 3] = fmaf(sv, xv.w, acc32[4 * c + 3]);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < RT; ++c)
+                    if (c < r) acc32[c] = fmaf(sv, x[col * r + c], acc32[c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < RT; ++c) {
+        float s, e;
+        two_sum(__int_as_float(__double2hiint(acc[c])), acc32[c], s, e);
+        const float l = __int_as_float(__double2loint(acc[c])) + e;
+        acc[c] = __hiloint2double(__float_as_int(s), __float_as_int(l));
     }
 }
 
@@ -973,8 +1024,17 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
             const int row = tid % nrows, g = tid / nrows;
             if (g < G) {
                 bool done = false;
+                if constexpr (!TC) {   // evaluated coupling blocks (FP32 operators)
+                    if (D.ptype == PIECE_NODES) {
+                        const int t = (int)((D.out_row - C.row_yhat) / C.kp);
+                        consume_nodes<RT>(stage_base + (size_t)st * a.stage_bytes, spc[st], D.npieces,
+                                          xbase + (size_t)st * kXin, r, C.nodes[(int64_t)t * C.kp + row], g, G,
+                                          acc);
+                        done = true;
+                    }
+                }
                 if constexpr (!TC && RT <= kTcCudaMaxRT) {   // tensor tiles on the CUDA cores (a.tc_cuda)
-                    if (piece_tc(D.ptype)) {
+                    if (!done && piece_tc(D.ptype)) {
                         consume_tc_tiles<RT>(stage_base + (size_t)st * a.stage_bytes, spc[st], D.npieces, D.ptype,
                                              xbase + (size_t)st * kXin, r, nrows, row, g, G, acc);
                         done = true;
@@ -1508,7 +1568,7 @@ static int launch_split(h2_handle* op, double* u2, int r, int rt, cudaStream_t s
     H2_CUDA_TRY(launch_near_rt<16>(na, op->nsm, nsmem, op->near_stream));
     KArgs a{};
     a.nops = 1;
-    a.ctx[0] = OpCtx{op->d_arena, ws, ws32, u2, op->d_perm, N, r, 0};
+    a.ctx[0] = OpCtx{op->d_arena, ws, ws32, u2, op->d_perm, N, r, op->kp, op->d_nodes, op->row_yhat};
     a.err = op->d_err;
     a.r = r;
     const FarCfg fc = split_far_cfg(op, rt);
@@ -1608,7 +1668,7 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
     }
     KArgs a{};
     a.nops = 1;
-    a.ctx[0] = OpCtx{op->d_arena, ws, ws32, u2, op->d_perm, N, r, 0};
+    a.ctx[0] = OpCtx{op->d_arena, ws, ws32, u2, op->d_perm, N, r, op->kp, op->d_nodes, op->row_yhat};
     a.err = op->d_err;
     a.r = r;
     a.stages = op_stages(op, rt);
@@ -2169,7 +2229,7 @@ int matvec_batched(h2_handle* const* ops, int n, const double* const* u1, double
     a.nops = n;
     for (int i = 0; i < n; ++i)
         a.ctx[i] = OpCtx{ops[i]->d_arena, ops[i]->d_ws, ops[i]->d_ws32, u2[i], ops[i]->d_perm, ops[i]->geom->N,
-                         (int)r[i], 0};
+                         (int)r[i], ops[i]->kp, ops[i]->d_nodes, ops[i]->row_yhat};
     a.err = ops[0]->d_err;
     a.r = rmax;
     a.stages = nst;

@@ -80,7 +80,8 @@ void emit_pass(h2_handle* op, const char* name, int32_t kind, std::vector<SegSpe
             // or BF16 hi + lo); column-major blocks otherwise
             const int Mp = tc_rows(s.nrows);
             const int kcols = tc ? (m.ncols + tc_kstep(m.type) - 1) / tc_kstep(m.type) * tc_kstep(m.type) : m.ncols;
-            const int64_t col_bytes = tc ? (int64_t)Mp * 4 : (int64_t)s.nrows * es;
+            // (evaluated coupling blocks: one float4 source node per column)
+            const int64_t col_bytes = tc ? (int64_t)Mp * 4 : m.type == PIECE_NODES ? 16 : (int64_t)s.nrows * es;
             const int64_t mbytes = round16(col_bytes * kcols);
             m.ref->off = arena;
             m.ref->nrows = s.nrows;
@@ -253,6 +254,7 @@ void build_plan(h2_handle* op) {
             });
         const int64_t nfar = (int64_t)op->far_t.size();
         const int split = op->coupling_split;
+        const int PS = op->params.coupling == H2_COUPLING_ON_THE_FLY ? PIECE_NODES : PT;   // coupling blocks
         std::vector<SegSpec> segs;
         for (int t = 0; t < nc; ++t) {
             if (by_t[t].empty()) continue;
@@ -264,7 +266,7 @@ void build_plan(h2_handle* op) {
                 s.mode = SEG_ATOMIC;
                 for (size_t g = g0; g < std::min(by_t[t].size(), g0 + split); ++g) {
                     const int32_t b = by_t[t][g];
-                    s.mats.push_back({&op->S[b], k, PT, xrow(op->far_s[b])});
+                    s.mats.push_back({&op->S[b], k, PS, xrow(op->far_s[b])});
                     s.bytes += (int64_t)k * k;
                 }
                 segs.push_back(s);

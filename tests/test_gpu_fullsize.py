@@ -23,13 +23,13 @@ import synth  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-8
-TOL = {"fp64": FP64_TOL, "fp32": 1e-5, "tf32x3": 1e-5}
+TOL = {"fp64": FP64_TOL, "fp32": 1e-5, "tf32x3": 1e-5, "fp32-onfly": 1e-5}
 # BF16 hi + lo stores about 17 significant bits (|a - hi - lo| <= 2^-17 |a|
 # with round-to-nearest hi and lo) against FP32's 24: its error is the FP32
 # form's error (the workload's amplification of per-entry rounding, measured
 # on the same rows) scaled by 2^(24 - 17), with a factor 2 of margin.
 BF16_OVER_FP32 = 2.0 * 2.0 ** (24 - 17)
-PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3}
+PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3, "fp32-onfly": 1}
 
 
 def sampled_rows(o):
@@ -51,14 +51,15 @@ def test_full_size_sampled_rows(name):
     g = pkg.Geometry(w.mesh.xyz, w.mesh.tri)
     x = torch.from_numpy(np.ascontiguousarray(w.u1)).cuda()
     errs = {}
-    for prec in ("fp64", "fp32", "tf32x3", "bf16x3"):
-        op = pkg.Operator(g, m=w.m, leaf=w.leaf, eta=w.eta, precision=PREC[prec], max_rhs=w.r)
+    for prec in ("fp64", "fp32", "tf32x3", "bf16x3", "fp32-onfly"):
+        op = pkg.Operator(g, m=w.m, leaf=w.leaf, eta=w.eta, precision=PREC[prec], max_rhs=w.r,
+                          coupling=pkg.COUPLING_ON_THE_FLY if prec == "fp32-onfly" else pkg.COUPLING_STORED)
         y = op.matvec(x, torch.full_like(x, float("nan"))).cpu().numpy()[:, rows]
         assert pkg.h2_device_status(op.handle) == 0
         errs[prec] = float(np.max(np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)))
         del op
         torch.cuda.empty_cache()
     print(name, {k: f"{v:.2e}" for k, v in errs.items()})
-    for prec in ("fp64", "fp32", "tf32x3"):
+    for prec in ("fp64", "fp32", "tf32x3", "fp32-onfly"):
         assert errs[prec] <= TOL[prec], (prec, errs[prec])
     assert errs["bf16x3"] <= BF16_OVER_FP32 * errs["fp32"], errs

@@ -141,6 +141,41 @@ def test_reduced_precision_matvec_within_budget(name, mk, m_, leaf, r, schedule,
     assert np.all(err <= REDUCED_TOL[precision]), err
 
 
+@pytest.mark.parametrize("schedule", sorted(SCHEDULES))
+@pytest.mark.parametrize("name,mk,m_,leaf,r", CASES, ids=[c[0] for c in CASES])
+def test_on_the_fly_coupling_within_budget(name, mk, m_, leaf, r, schedule):
+    """FP32 operator whose coupling blocks S_ts(nu, mu) = 1 / (4 pi |x_nu - y_mu|)
+    are evaluated in the product from the Chebyshev nodes instead of stored:
+    relative error <= 1e-5 against the FP64 oracle (which stores S exactly), and
+    no coupling matrix is streamed."""
+    m = mk()
+    x = _inputs(m, r)
+    g = pkg.Geometry(m.xyz, m.tri)
+    op = pkg.Operator(g, m=m_, leaf=leaf, max_rhs=r, precision=pkg.FP32, schedule=SCHEDULES[schedule],
+                      coupling=pkg.COUPLING_ON_THE_FLY)
+    stored = pkg.Operator(g, m=m_, leaf=leaf, max_rhs=r, precision=pkg.FP32, schedule=SCHEDULES[schedule])
+    xd = torch.from_numpy(x).cuda()
+    y = op.matvec(xd, nan_out(xd)).cpu().numpy()
+    assert pkg.h2_device_status(op.handle) == 0
+    ref = oracle.H2Oracle(m.xyz, m.tri, m_, leaf, 2.0).matvec(x)
+    err = rel_err(y, ref)
+    assert np.all(err <= MIXED_TOL), err
+    k = m_ ** 3
+    st, ss = op.stats(), stored.stats()
+    if st["n_far_blocks"]:
+        # each coupling block streams k source nodes (16 bytes) instead of k x k FP32 entries
+        saved = ss["bytes_streamed"] - st["bytes_streamed"]
+        assert saved >= st["n_far_blocks"] * (4 * k * k - 16 * k) - 16 * st["n_far_blocks"], (saved, st["n_far_blocks"])
+
+
+def test_on_the_fly_coupling_needs_an_fp32_operator():
+    m = synth.icosphere(2)
+    g = pkg.Geometry(m.xyz, m.tri)
+    for prec in (pkg.FP64, pkg.TF32X3, pkg.BF16X3):
+        with pytest.raises(pkg.H2Error):
+            pkg.Operator(g, m=3, leaf=16, precision=prec, coupling=pkg.COUPLING_ON_THE_FLY)
+
+
 def test_all_near_operator_is_the_dense_matrix():
     # eta -> 0: nothing is admissible, every block is an exact near block
     m = synth.icosphere(2)
