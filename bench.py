@@ -151,6 +151,23 @@ def cpu_oracle_rate(mesh, m, leaf, eta, u1, budget_s: float):
     return rate, oracle.num_threads(), n, el, setup, y
 
 
+def max_over_ranks(t: float, dist, device) -> float:
+    """The slowest rank's time (the job's time: every rank's step ends behind
+    a barrier); `dist` None is a single process."""
+    if dist is None:
+        return t
+    import torch
+    x = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return float(x.item())
+
+
+def replica_rate(units_per_rank: float, world: int, t_job: float) -> float:
+    """Whole-job throughput of `world` replicas, each processing
+    `units_per_rank` units per step, with the job's step time."""
+    return units_per_rank * world / t_job
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -271,11 +288,8 @@ def run_gpu(args, rank, local, world):
     with ClockSampler(local) as clk:
         op, x, y, t_step = time_form(pkg, torch, g, w, u1_np, args.precision, args.schedule, args.steps,
                                      args.warmup, barrier)
-    if dist is not None:
-        t = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
-    value = N * r * world / t_step
+    t_step = max_over_ranks(t_step, dist, "cuda")
+    value = replica_rate(N * r, world, t_step)
     st = op.stats()
     stream = torch.cuda.current_stream()
     sp = int(stream.cuda_stream)
@@ -294,11 +308,7 @@ def run_gpu(args, rank, local, world):
         pkg.h2_matvec(op.handle, xh.data_ptr(), yh.data_ptr(), r, sp)
     e1.record(stream)
     torch.cuda.synchronize()
-    t_e2e = e0.elapsed_time(e1) / 1e3 / args.steps
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3 / args.steps, dist, "cuda")
 
     passes = pass_profile(pkg, op, x, y, r, args.steps)
     y_np = y.cpu().numpy()
@@ -404,7 +414,7 @@ def run_gpu(args, rank, local, world):
                    "l2": f"inputs larger than L2: {st['bytes_streamed'] / 1e6:.0f} MB of matrices "
                          f"streamed per step (L2 129 MB), no flush"},
         "clocks": clocks,
-        "e2e": {"value": N * r * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * N * r,
+        "e2e": {"value": replica_rate(N * r, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": 8 * N * r,
                 "d2h_bytes_per_step": 8 * N * r},
         "gpu_launches": st["n_launches_matvec"] * args.steps,
         "rel_err_vs_fp64_oracle": rel_err(y_np, refs[r]) if r in refs else None,
