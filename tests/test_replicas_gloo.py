@@ -39,7 +39,7 @@ def _rank(rank, world, port, times, out):
 def test_slowest_rank_sets_the_job_time_and_every_rank_counts():
     world = 2
     times = [0.25, 0.4]
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank, args=(world, _free_port(), times, out), nprocs=world, join=True)
         res = dict(out)
