@@ -41,15 +41,17 @@ FP32_FMA_PER_CLK_SM = 128
 PASS_NAMES = {0: "gather", 1: "up_leaf", 2: "up_transfer", 3: "coupling", 4: "down_transfer",
               5: "leaf_near", 6: "leaf_expand", 7: "flow"}
 
-# fp32-onfly: FP32 far field with the coupling blocks evaluated in the product
-PRECISIONS = ("fp64", "fp32", "tf32x3", "bf16x3", "fp32-onfly")
+# fp32-onfly: FP32 far field with the coupling blocks evaluated in the product;
+# fp32-pair, bf16x3-pair: the near field of split-form products (r > 8) in
+# FP32 pairs with error-free products and sums (FP64-equivalent, ~1e-13)
+PRECISIONS = ("fp64", "fp32", "tf32x3", "bf16x3", "fp32-onfly", "fp32-pair", "bf16x3-pair")
 DTYPES = {"fp64": "f64", "fp32": "f32+f64", "tf32x3": "tf32x3+f64", "bf16x3": "bf16x3+f64",
-          "fp32-onfly": "f32+f64"}
+          "fp32-onfly": "f32+f64", "fp32-pair": "f32+f32x2+f64", "bf16x3-pair": "bf16x3+f32x2+f64"}
 # reduced-precision and batched forms timed beside the headline form (same
 # workload, same GPU): (precision, right-hand sides)
 FORMS = [("fp32", 1), ("tf32x3", 1), ("bf16x3", 1), ("fp32-onfly", 1), ("fp64", 32), ("fp32", 32),
          ("fp32-onfly", 32), ("tf32x3", 32),
-         ("bf16x3", 32)]
+         ("bf16x3", 32), ("fp32-pair", 32), ("bf16x3-pair", 32)]
 
 
 def workload_inputs(name: str, r: int):
@@ -201,10 +203,13 @@ def time_form(pkg, torch, g, w, u1_np, precision, schedule, steps, warmup, barri
     """Builds the operator of one form and times `steps` matvecs with CUDA
     events on the launching stream (inputs resident in device memory)."""
     r = u1_np.shape[0]
+    base = precision.split("-")[0]
+    pair = precision.endswith("-pair") and r > 8   # the paired near field needs split-form products
     op = pkg.Operator(g, m=w.m, leaf=w.leaf, eta=w.eta, precision={"fp64": pkg.FP64, "fp32": pkg.FP32,
-                      "tf32x3": pkg.TF32X3, "bf16x3": pkg.BF16X3, "fp32-onfly": pkg.FP32}[precision], max_rhs=r,
+                      "tf32x3": pkg.TF32X3, "bf16x3": pkg.BF16X3}[base], max_rhs=r,
                       schedule=pkg.SCHEDULE_FLOW if schedule == "flow" else pkg.SCHEDULE_LEVELS,
-                      coupling=pkg.COUPLING_ON_THE_FLY if precision == "fp32-onfly" else pkg.COUPLING_STORED)
+                      coupling=pkg.COUPLING_ON_THE_FLY if precision == "fp32-onfly" else pkg.COUPLING_STORED,
+                      near_field=pkg.NEAR_F32PAIR if pair else pkg.NEAR_FP64)
     stream = torch.cuda.current_stream()
     sp = int(stream.cuda_stream)
     x = torch.from_numpy(u1_np).cuda()

@@ -85,7 +85,7 @@ typedef struct {
     int32_t schedule;       /* h2_schedule: how one h2_matvec is launched              */
     int32_t autotune;       /* 1: h2_assemble ends with h2_autotune(op, max_rhs)       */
     int32_t coupling;       /* h2_coupling: stored S_ts (default) or evaluated        */
-    int32_t reserved[1];    /* must be zero                                           */
+    int32_t near_field;     /* h2_near_field: near-field arithmetic (default FP64)     */
 } h2_params;
 
 /* H2_COUPLING_STORED (default): the coupling matrices S_ts are assembled and
@@ -98,6 +98,27 @@ typedef struct {
  *   matrices, the largest part of the far field, are neither stored nor
  *   streamed. */
 typedef enum { H2_COUPLING_STORED = 0, H2_COUPLING_ON_THE_FLY = 1 } h2_coupling;
+
+/* Arithmetic of the near-field product y|_t += sum_s N_ts x|_s (the exact
+ * Lindholm blocks of the inadmissible leaf pairs, Section "H2-Matrix
+ * Compression": only the admissible blocks are approximated).
+ * H2_NEAR_FP64 (default): FP64 entries, FP64 products and sums.
+ * H2_NEAR_F32PAIR (H2_FP32 and H2_BF16X3 operators with max_rhs > 8): the
+ *   products that run in the split form (more than 8 right-hand sides, see
+ *   h2_params.max_rhs) carry every near-field entry and input value as an
+ *   unevaluated pair of FP32 numbers hi + lo (hi = fp32(v), lo = fp32(v - hi):
+ *   48 significant bits) and multiply them with error-free transformations on
+ *   the FP32 pipe, which GB300 runs at 64 times its FP64 rate: the exact
+ *   product hi_a*hi_x as a rounded product and its FMA-computed error
+ *   (Dekker 1971), the cross terms hi_a*lo_x + lo_a*hi_x, and a running sum
+ *   kept as a rounded sum plus its TwoSum error (Knuth 1969).  Each leaf's
+ *   result is converted to FP64 once and added to the FP64 output.  The
+ *   relative error of one row's sum stays near 2^-48 times the sum of the
+ *   magnitudes of its terms (about 1e-13 on the benchmark meshes), far inside
+ *   the reduced forms' 1e-5.  A paired copy of the near blocks is kept beside
+ *   the FP64 ones (the same bytes again), which products with at most 8
+ *   right-hand sides still use. */
+typedef enum { H2_NEAR_FP64 = 0, H2_NEAR_F32PAIR = 1 } h2_near_field;
 
 /* H2_SCHEDULE_FLOW (default): one persistent kernel after the input gather;
  *   its CTAs take the product's segments in a dependency order and wait

@@ -17,6 +17,8 @@ SCHEDULE_FLOW = 0
 SCHEDULE_LEVELS = 1
 COUPLING_STORED = 0
 COUPLING_ON_THE_FLY = 1
+NEAR_FP64 = 0
+NEAR_F32PAIR = 1
 
 _LIB = None
 _LOCK = threading.Lock()
@@ -42,7 +44,7 @@ class Params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("leaf", ctypes.c_int32), ("eta", ctypes.c_double),
                 ("box_inflation", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("max_rhs", ctypes.c_int32), ("schedule", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("coupling", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("autotune", ctypes.c_int32), ("coupling", ctypes.c_int32), ("near_field", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):
@@ -274,12 +276,13 @@ class Operator:
     def __init__(self, geom: Geometry, m: int = 4, leaf: int = 64, eta: float = 2.0,
                  rho: float = 0.25, precision: int = FP64, max_rhs: int = 1,
                  schedule: int = SCHEDULE_FLOW, autotune: bool = False,
-                 coupling: int = COUPLING_STORED):
+                 coupling: int = COUPLING_STORED, near_field: int = NEAR_FP64):
         self.geom = geom
         self.N = geom.N
         self.params = h2_default_params(m=m, leaf=leaf, eta=eta, box_inflation=rho,
                                         precision=precision, max_rhs=max_rhs, schedule=schedule,
-                                        autotune=1 if autotune else 0, coupling=coupling)
+                                        autotune=1 if autotune else 0, coupling=coupling,
+                                        near_field=near_field)
         self.handle = h2_assemble(geom.handle, self.params)
 
     def autotune(self, r: int | None = None, stream=None) -> dict:

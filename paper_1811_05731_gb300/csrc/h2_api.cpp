@@ -32,7 +32,7 @@ void free_device(h2_handle* h) {
         f(h->d_fseg); f(h->d_fchunk); f(h->d_fpiece); f(h->d_fdeps); f(h->d_fexpect); f(h->d_fzero_rows);
         f(h->d_fcnt);
         f(h->d_sseg); f(h->d_schunk); f(h->d_spiece); f(h->d_sdeps); f(h->d_sexpect); f(h->d_szero_rows);
-        f(h->d_u2n); f(h->d_near_units); f(h->d_nodes);
+        f(h->d_u2n); f(h->d_near_units); f(h->d_nodes); f(h->d_near_pair); f(h->d_wsp);
         if (h->near_stream) cudaStreamDestroy(h->near_stream);
         if (h->ev_fork) cudaEventDestroy(h->ev_fork);
         if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -134,7 +134,10 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
     if (p.autotune != 0 && p.autotune != 1) return H2_ERR_INVALID_ARG;
     if (p.coupling != H2_COUPLING_STORED && p.coupling != H2_COUPLING_ON_THE_FLY) return H2_ERR_INVALID_ARG;
     if (p.coupling == H2_COUPLING_ON_THE_FLY && p.precision != H2_FP32) return H2_ERR_INVALID_ARG;
-    if (p.reserved[0] != 0) return H2_ERR_INVALID_ARG;
+    if (p.near_field != H2_NEAR_FP64 && p.near_field != H2_NEAR_F32PAIR) return H2_ERR_INVALID_ARG;
+    if (p.near_field == H2_NEAR_F32PAIR &&
+        ((p.precision != H2_FP32 && p.precision != H2_BF16X3) || p.max_rhs <= 8))
+        return H2_ERR_INVALID_ARG;
     const auto t0 = std::chrono::steady_clock::now();
     h2_handle* geom = const_cast<h2_handle*>(geom_c);
     h2_handle* op = new (std::nothrow) h2_handle();

@@ -436,6 +436,17 @@ struct NearItem {
 // One near block N_ts (|t| x |s| column-major: (a, b) at b*|t| + a) per CTA;
 // thread a owns row a and sums the corner weights of every triangle around
 // the source leaf into the columns of the corners that belong to s.
+// The paired copy of the near blocks (h2_near_field H2_NEAR_F32PAIR): every
+// FP64 value v of the near pass's arena bytes as hi = fp32(v) and
+// lo = fp32(v - hi), the exact remainder rounded once (48 significant bits).
+__global__ void k_pair_split(const double* __restrict__ src, float2* __restrict__ dst, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = src[i];
+        const float hi = __double2float_rn(v);
+        dst[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+}
+
 __global__ void k_near(const NearItem* __restrict__ items, const LeafTri* __restrict__ ltri,
                        const int32_t* __restrict__ perm, const double* __restrict__ xyz,
                        const int32_t* __restrict__ tri, const double* __restrict__ psi,
@@ -646,6 +657,12 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
         const int nb = (maxleaf + 31) / 32 * 32;
         k_near<<<(unsigned)ni.size(), nb, smem, s>>>(d_ni, d_lt, op->d_perm, g->d_xyz, g->d_tri,
                                                      g->d_psi, op->d_arena);
+    }
+    if (op->d_near_pair && op->near_hi > op->near_lo) {
+        const int64_t n = (op->near_hi - op->near_lo) / 8;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16 * 152));
+        k_pair_split<<<grid, 256, 0, s>>>(reinterpret_cast<const double*>(op->d_arena + op->near_lo),
+                                          op->d_near_pair, n);
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

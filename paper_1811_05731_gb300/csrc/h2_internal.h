@@ -282,6 +282,12 @@ struct h2_handle {
     std::vector<std::array<int32_t, 4>> near_units;   // near-field work units: segment, first chunk, chunks
     int4* d_near_units = nullptr;
     float4* d_nodes = nullptr;        // evaluated coupling: kp Chebyshev nodes per cluster, minus its box's centre
+    // paired near field (h2_near_field H2_NEAR_F32PAIR, split form only):
+    // the near pass's arena bytes [near_lo, near_hi) again, every FP64 value
+    // as two FP32 words hi, lo; the input rows as pairs, laid out like d_ws
+    float2* d_near_pair = nullptr;
+    int64_t near_lo = 0, near_hi = 0;
+    float2* d_wsp = nullptr;
     cudaStream_t near_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // per-pass timing with CUDA events (profiling aid, off by default)

@@ -32,6 +32,7 @@
 #include <cstring>
 #include <memory>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "h2_internal.h"
@@ -1118,14 +1119,34 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
 constexpr int kNearCons = 256;
 constexpr int kNearBlock = kNearCons + 32;
 
+// One term a*x of a paired near-field sum hi + lo (h2_near_field
+// H2_NEAR_F32PAIR; a, x = (hi, lo) FP32 pairs): the product of the high words
+// is split exactly into its rounded value p and error e (an FMA gives e,
+// Dekker 1971); p enters hi through TwoSum (Knuth), whose error, e and the
+// cross terms a.hi*x.lo + a.lo*x.hi go to lo (a.lo*x.lo, below 2^-48 of the
+// term, is left out).  p is taken with __fmul_rn so that the compiler cannot
+// contract it into the sum.
+__device__ __forceinline__ void pair_fma(float2 a, float2 x, float& hi, float& lo) {
+    const float p = __fmul_rn(a.x, x.x);
+    const float e = fmaf(a.x, x.x, -p);
+    float s, t;
+    two_sum(hi, p, s, t);
+    hi = s;
+    lo = fmaf(a.x, x.y, lo);
+    lo = fmaf(a.y, x.x, lo);
+    lo += e + t;
+}
+
 struct NArgs {
     const FlowSeg* seg;     // the near pass's segments (leaves, <= 64 rows)
     const Chunk* chunk;
     const Piece* piece;
     const int4* units;      // work units: segment, first chunk in it, chunks
     int nunits;
-    const unsigned char* arena;
-    const double* ws;       // FP64 workspace: input rows in tree order
+    const unsigned char* arena;   // chunk c's bytes at arena + (c.src - src_base)
+    int64_t src_base;
+    const unsigned char* xsrc;    // input rows in tree order, 8 bytes per value:
+                                  // FP64, or an FP32 pair (hi, lo) when PAIR
     double* u2n;            // r x N
     const int32_t* perm;
     int64_t N;
@@ -1142,7 +1163,7 @@ struct NStage {
 // At most 40 registers per thread: one CTA of this kernel and one of the
 // far-field launch at r <= 16 (288 threads x 128 registers) share each SM
 // sub-partition's 16 K registers even where three warps of each meet.
-template <int RT>
+template <int RT, bool PAIR>
 __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
     constexpr int JM = RT / 4;   // items per thread: 64 rows x RT / 256 threads
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1206,7 +1227,8 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
                 const Chunk ch = a.chunk[F.chunk0 + U.y + ci];
                 if (lane == 0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    tma_load(stage_base + (size_t)st * a.stage_bytes, a.arena + ch.src, (uint32_t)ch.bytes, &full[st]);
+                    tma_load(stage_base + (size_t)st * a.stage_bytes, a.arena + (ch.src - a.src_base),
+                             (uint32_t)ch.bytes, &full[st]);
                 }
                 ++issued;
                 Piece pc{};
@@ -1231,7 +1253,7 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
                     asm volatile(
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                             smem_addr(xbase + (size_t)st * kXin + xoff)),
-                        "l"(a.ws + (int64_t)pc.in_row * r), "r"(mine), "r"(smem_addr(&full[st]))
+                        "l"(a.xsrc + (int64_t)pc.in_row * r * 8), "r"(mine), "r"(smem_addr(&full[st]))
                         : "memory");
                 }
                 if (lane == 0) {
@@ -1243,8 +1265,13 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
     } else {
         // ---------------- consumer warps ----------------
         double acc[JM];
+        float hi[JM], lo[JM];   // PAIR: each item's running sum hi + lo
 #pragma unroll
-        for (int j = 0; j < JM; ++j) acc[j] = 0.0;
+        for (int j = 0; j < JM; ++j) {
+            acc[j] = 0.0;
+            hi[j] = 0.0f;
+            lo[j] = 0.0f;
+        }
         int cur = -1, nitems = 0, nrows = 1;
         int irow[JM], icol[JM];   // item j of this thread: output row, right-hand side
         for (int i = 0;; ++i) {
@@ -1271,24 +1298,40 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
             const unsigned char* xin = xbase + (size_t)st * kXin;
             for (int p = 0; p < D.npieces; ++p) {
                 const SPiece P = spc[st][p];
-                const double* A = reinterpret_cast<const double*>(stg + P.smem_off);
-                const double* x = reinterpret_cast<const double*>(xin + P.xoff);
+                if constexpr (PAIR) {
+                    const float2* A = reinterpret_cast<const float2*>(stg + P.smem_off);
+                    const float2* x = reinterpret_cast<const float2*>(xin + P.xoff);
 #pragma unroll 2
-                for (int col = 0; col < P.ncols; ++col) {
-                    const double* Ac = A + col * nrows;
-                    const double* xc = x + col * r;
+                    for (int col = 0; col < P.ncols; ++col) {
+                        const float2* Ac = A + col * nrows;
+                        const float2* xc = x + col * r;
 #pragma unroll
-                    for (int j = 0; j < JM; ++j)
-                        if (tid + kNearCons * j < nitems) acc[j] = fma(Ac[irow[j]], xc[icol[j]], acc[j]);
+                        for (int j = 0; j < JM; ++j)
+                            if (tid + kNearCons * j < nitems) pair_fma(Ac[irow[j]], xc[icol[j]], hi[j], lo[j]);
+                    }
+                } else {
+                    const double* A = reinterpret_cast<const double*>(stg + P.smem_off);
+                    const double* x = reinterpret_cast<const double*>(xin + P.xoff);
+#pragma unroll 2
+                    for (int col = 0; col < P.ncols; ++col) {
+                        const double* Ac = A + col * nrows;
+                        const double* xc = x + col * r;
+#pragma unroll
+                        for (int j = 0; j < JM; ++j)
+                            if (tid + kNearCons * j < nitems) acc[j] = fma(Ac[irow[j]], xc[icol[j]], acc[j]);
+                    }
                 }
             }
             mbar_arrive(&empty[st]);
             if (D.last) {
 #pragma unroll
                 for (int j = 0; j < JM; ++j) {
+                    const double v = PAIR ? (double)hi[j] + (double)lo[j] : acc[j];
                     if (tid + kNearCons * j < nitems)
-                        atomicAdd(a.u2n + (int64_t)icol[j] * a.N + a.perm[D.out_row + irow[j]], acc[j]);
+                        atomicAdd(a.u2n + (int64_t)icol[j] * a.N + a.perm[D.out_row + irow[j]], v);
                     acc[j] = 0.0;
+                    hi[j] = 0.0f;
+                    lo[j] = 0.0f;
                 }
             }
         }
@@ -1308,11 +1351,12 @@ __global__ void k_add(double* __restrict__ u2, const double* __restrict__ u2n, i
 }
 
 // Gathers the input into the workspace's input rows (leaf by leaf in tree
-// order, padding rows zero) in FP64 and, for FP32 operators, in FP32; clears
+// order, padding rows zero) in FP64 and, for FP32 operators, in FP32 and, for
+// a paired near field, as FP32 pairs hi = fp32(v), lo = fp32(v - hi); clears
 // the y-hat rows that are accumulated atomically (in the workspace of the
 // far field); clears `nclear` ints (the flow kernel's counters).
 __global__ void k_prologue(const double* __restrict__ u1, double* __restrict__ ws, float* __restrict__ ws32,
-                           const int32_t* __restrict__ gsrc, int64_t nrows_in, int64_t N, int r,
+                           float2* __restrict__ wsp, const int32_t* __restrict__ gsrc, int64_t nrows_in, int64_t N, int r,
                            const int32_t* __restrict__ zero_rows, int nzero, int kp, int32_t* __restrict__ clear,
                            int nclear) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1324,6 +1368,10 @@ __global__ void k_prologue(const double* __restrict__ u1, double* __restrict__ w
         const double v = src >= 0 ? u1[c * N + src] : 0.0;
         ws[idx] = v;
         if (ws32) ws32[idx] = (float)v;
+        if (wsp) {
+            const float h = __double2float_rn(v);
+            wsp[idx] = make_float2(h, __double2float_rn(v - (double)h));
+        }
     }
     const int64_t per = (int64_t)kp * r;
     const int64_t totz = (int64_t)nzero * per;
@@ -1352,14 +1400,21 @@ int rt_for(int r) {
 
 // Allows `smem` bytes of dynamic shared memory and asks for the largest
 // shared-memory carveout, so that as many CTAs as fit are resident per SM.
+// One record per kernel for every path that launches or sizes it: a path with
+// a record of its own could lower the kernel's limit below what another
+// path's record still assumes, and that path's next launch would fail.
 template <class F>
-cudaError_t set_smem(F* kernel, size_t smem, size_t& configured) {
-    if (configured >= smem) return cudaSuccess;
+cudaError_t set_smem(F* kernel, size_t smem) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, size_t> configured;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& c = configured[reinterpret_cast<const void*>(kernel)];
+    if (c >= smem) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
-    if (e == cudaSuccess) configured = smem;
+    if (e == cudaSuccess) c = smem;
     return e;
 }
 
@@ -1381,9 +1436,9 @@ int ctas_per_sm(F* kernel, size_t smem, int& cached, size_t& cached_smem) {
 // *launched receives the grid size.
 template <int RT, bool FLOW, bool TC>
 cudaError_t launch_seg_rt(const KArgs& a, int nsm, size_t smem, cudaStream_t s, int* launched, int cap) {
-    static size_t configured = 0, occ_smem = 0;
+    static size_t occ_smem = 0;
     static int occ = 0;
-    cudaError_t e = set_smem(k_seg<RT, FLOW, TC>, smem, configured);
+    cudaError_t e = set_smem(k_seg<RT, FLOW, TC>, smem);
     if (e != cudaSuccess) return e;
     int per_sm = ctas_per_sm(k_seg<RT, FLOW, TC>, smem, occ, occ_smem);
     if (cap > 0 && cap < per_sm) per_sm = cap;   // the autotuner's CTA count
@@ -1410,8 +1465,7 @@ cudaError_t launch_seg_rt(const KArgs& a, int nsm, size_t smem, cudaStream_t s, 
 
 template <int RT, bool TC>
 int seg_occupancy(size_t smem) {
-    static size_t configured = 0;
-    if (set_smem(k_seg<RT, true, TC>, smem, configured) != cudaSuccess) {
+    if (set_smem(k_seg<RT, true, TC>, smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -1525,12 +1579,11 @@ static size_t split_far_smem(const h2_handle* op, int rt) {
     return seg_smem_raw(rt, c.stages, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op), c.sets);
 }
 
-template <int RT>
+template <int RT, bool PAIR>
 cudaError_t launch_near_rt(const NArgs& a, int nsm, size_t smem, cudaStream_t s) {
-    static size_t configured = 0;
-    cudaError_t e = set_smem(k_near_items<RT>, smem, configured);
+    cudaError_t e = set_smem(k_near_items<RT, PAIR>, smem);
     if (e != cudaSuccess) return e;
-    k_near_items<RT><<<nsm, kNearBlock, smem, s>>>(a);
+    k_near_items<RT, PAIR><<<nsm, kNearBlock, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1553,8 +1606,10 @@ static int launch_split(h2_handle* op, double* u2, int r, int rt, cudaStream_t s
     na.piece = np->d_piece;
     na.units = op->d_near_units;
     na.nunits = (int)op->near_units.size();
-    na.arena = op->d_arena;
-    na.ws = ws;
+    const bool pair = op->d_near_pair != nullptr;   // paired near field (blocks and inputs)
+    na.arena = pair ? reinterpret_cast<const unsigned char*>(op->d_near_pair) : op->d_arena;
+    na.src_base = pair ? op->near_lo : 0;
+    na.xsrc = pair ? reinterpret_cast<const unsigned char*>(op->d_wsp) : reinterpret_cast<const unsigned char*>(ws);
     na.u2n = op->d_u2n;
     na.perm = op->d_perm;
     na.N = N;
@@ -1565,7 +1620,8 @@ static int launch_split(h2_handle* op, double* u2, int r, int rt, cudaStream_t s
     na.err = op->d_err;
     const size_t nsmem = near_smem_bytes(op, rt);
     if (rt != 16) return H2_ERR_INVALID_ARG;   // split products have 9..16 right-hand sides
-    H2_CUDA_TRY(launch_near_rt<16>(na, op->nsm, nsmem, op->near_stream));
+    if (pair) H2_CUDA_TRY((launch_near_rt<16, true>(na, op->nsm, nsmem, op->near_stream)));
+    else H2_CUDA_TRY((launch_near_rt<16, false>(na, op->nsm, nsmem, op->near_stream)));
     KArgs a{};
     a.nops = 1;
     a.ctx[0] = OpCtx{op->d_arena, ws, ws32, u2, op->d_perm, N, r, op->kp, op->d_nodes, op->row_yhat};
@@ -1655,7 +1711,8 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
         const int nclear = flow ? 3 * op->nc + 2 : 0;
         const int64_t work = std::max<int64_t>({op->row_xhat * r, (int64_t)zr.size() * op->kp * r, (int64_t)nclear});
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 4096));
-        k_prologue<<<grid, 256, 0, s>>>(u1, ws, ws32, op->d_gather_src, op->row_xhat, N, r, d_zr, (int)zr.size(),
+        float2* wsp = split && op->d_near_pair ? op->d_wsp : nullptr;
+        k_prologue<<<grid, 256, 0, s>>>(u1, ws, ws32, wsp, op->d_gather_src, op->row_xhat, N, r, d_zr, (int)zr.size(),
                                         op->kp, op->d_fcnt, nclear);
         H2_CUDA_TRY(cudaGetLastError());
     }
@@ -1887,6 +1944,21 @@ int upload_plan(h2_handle* op) {
         H2_CUDA_TRY(cudaStreamCreateWithFlags(&op->near_stream, cudaStreamNonBlocking));
         H2_CUDA_TRY(cudaEventCreateWithFlags(&op->ev_fork, cudaEventDisableTiming));
         H2_CUDA_TRY(cudaEventCreateWithFlags(&op->ev_join, cudaEventDisableTiming));
+        if (op->params.near_field == H2_NEAR_F32PAIR) {
+            // the near pass's contiguous arena range, paired by the assembly
+            const Pass* np = nullptr;
+            for (const Pass& q : op->passes)
+                if (q.kind == PASS_LEAF_NEAR) np = &q;
+            op->near_lo = INT64_MAX;
+            op->near_hi = 0;
+            for (const Chunk& c : np->chunk) {
+                op->near_lo = std::min<int64_t>(op->near_lo, c.src);
+                op->near_hi = std::max<int64_t>(op->near_hi, c.src + c.bytes);
+            }
+            if (op->near_hi <= op->near_lo) op->near_lo = op->near_hi = 0;
+            H2_CUDA_TRY(cudaMalloc((void**)&op->d_near_pair, (size_t)std::max<int64_t>(16, op->near_hi - op->near_lo)));
+            H2_CUDA_TRY(cudaMalloc((void**)&op->d_wsp, sizeof(float2) * (size_t)op->ws_rows * op->params.max_rhs));
+        }
     }
     if ((rc = upload_vec(op->gather_src, &op->d_gather_src))) return rc;
     H2_CUDA_TRY(cudaMalloc((void**)&op->d_ws, sizeof(double) * (size_t)op->ws_rows * op->params.max_rhs));
@@ -2221,7 +2293,7 @@ int matvec_batched(h2_handle* const* ops, int n, const double* const* u1, double
         const int64_t work =
             std::max<int64_t>({op->row_xhat * r[i], (int64_t)zr.size() * op->kp * r[i], (int64_t)nclear});
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 4096));
-        k_prologue<<<grid, 256, 0, s>>>(u1[i], op->d_ws, op->d_ws32, op->d_gather_src, op->row_xhat, op->geom->N,
+        k_prologue<<<grid, 256, 0, s>>>(u1[i], op->d_ws, op->d_ws32, nullptr, op->d_gather_src, op->row_xhat, op->geom->N,
                                         r[i], bp->d_zero[i], (int)zr.size(), op->kp, bp->d_cnt, nclear);
         H2_CUDA_TRY(cudaGetLastError());
     }

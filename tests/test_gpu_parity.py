@@ -300,6 +300,63 @@ def test_split_form_runs_and_matches_oracle(precision):
         assert err <= REDUCED_TOL[precision], (r, err)
 
 
+def test_paired_near_field_all_near_operator_is_the_dense_matrix():
+    """eta -> 0 leaves only exact near blocks, so the product is the dense M.
+    With the paired near field (FP32 pairs, error-free products and sums) an
+    FP32 operator's split-form products still match x M^T to 1e-12, which a
+    near field summed in plain FP32 (errors near 1e-7) would miss."""
+    m = synth.icosphere(2)
+    g = pkg.Geometry(m.xyz, m.tri)
+    M = oracle.dense_matrix(m.xyz, m.tri)
+    op = pkg.Operator(g, m=3, leaf=16, eta=1e-9, max_rhs=12, precision=pkg.FP32,
+                      near_field=pkg.NEAR_F32PAIR)
+    assert op.stats()["n_far_blocks"] == 0
+    assert op.stats()["n_launches_matvec"] == 4
+    x = np.vstack([synth.gaussian_rhs(m.n_vertices, 11, 3), np.ones((1, m.n_vertices))])
+    xt = torch.from_numpy(x).cuda()
+    for _ in range(3):   # direct launch, graph capture, graph replay
+        y = op.matvec(xt, nan_out(xt)).cpu().numpy()
+        assert pkg.h2_device_status(op.handle) == 0
+        assert np.max(np.abs(y - x @ M.T)) < 1e-12
+        assert np.max(np.abs(y[-1] + 1.0)) < 1e-12   # Gauss: M 1 = -1
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_paired_near_field_within_budget(precision):
+    """The paired near field in the split form with a far field: the product
+    meets the budget against the oracle for r at and below the operator's
+    maximum (split products at 24, 17 and 9; 3 runs the FP64 near field), and
+    stays within FP32 rounding of the same operator with the FP64 near field."""
+    m = synth.cube_sphere(9)
+    g = pkg.Geometry(m.xyz, m.tri)
+    op = pkg.Operator(g, m=4, leaf=20, max_rhs=24, precision=PRECISIONS[precision],
+                      near_field=pkg.NEAR_F32PAIR)
+    op64 = pkg.Operator(g, m=4, leaf=20, max_rhs=24, precision=PRECISIONS[precision])
+    assert op.stats()["n_launches_matvec"] == 4 + 2
+    o = oracle.H2Oracle(m.xyz, m.tri, 4, 20, 2.0)
+    for r in (24, 17, 9, 3):
+        x = _inputs(m, r, seed=17)
+        ref = o.matvec(x)
+        xt = torch.from_numpy(x).cuda()
+        y = op.matvec(xt, nan_out(xt)).cpu().numpy()
+        y64 = op64.matvec(xt).cpu().numpy()
+        assert pkg.h2_device_status(op.handle) == 0
+        nrm = np.linalg.norm(ref, axis=1)
+        err = np.max(np.linalg.norm(y - ref, axis=1) / nrm)
+        assert err <= REDUCED_TOL[precision], (r, err)
+        assert np.max(np.linalg.norm(y - y64, axis=1) / nrm) <= 1e-6, r
+
+
+def test_paired_near_field_needs_a_split_capable_operator():
+    m = synth.icosphere(2)
+    g = pkg.Geometry(m.xyz, m.tri)
+    for prec, max_rhs in ((pkg.FP64, 16), (pkg.TF32X3, 16), (pkg.FP32, 8), (pkg.BF16X3, 1)):
+        with pytest.raises(pkg.H2Error):
+            pkg.Operator(g, m=3, leaf=16, precision=prec, max_rhs=max_rhs, near_field=pkg.NEAR_F32PAIR)
+    with pytest.raises(pkg.H2Error):
+        pkg.Operator(g, m=3, leaf=16, precision=pkg.FP32, max_rhs=16, near_field=2)
+
+
 def test_autotuner_with_split_and_tile_pipe_candidates():
     """The autotuner's extra candidates (the split form above 8 right-hand sides;
     the CUDA-core / tensor-core pipe for 3xTF32 tiles at r <= 4) keep the product
