@@ -1166,6 +1166,7 @@ struct NStage {
 template <int RT, bool PAIR>
 __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
     constexpr int JM = RT / 4;   // items per thread: 64 rows x RT / 256 threads
+    static_assert(!PAIR || JM >= 4, "paired form: four right-hand sides per thread");
     extern __shared__ __align__(128) unsigned char smem[];
     const int S = a.stages;
     constexpr size_t kXin = xin_bytes(RT);
@@ -1274,6 +1275,10 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
         }
         int cur = -1, nitems = 0, nrows = 1;
         int irow[JM], icol[JM];   // item j of this thread: output row, right-hand side
+        // PAIR: one output row and up to four consecutive right-hand sides per
+        // thread (64 rows x 16 right-hand sides fill the 256 threads), so that
+        // one entry load serves four products
+        int prow = 0, prhs0 = 0, pcnt = 0;
         for (int i = 0;; ++i) {
             const int st = i % S;
             if (!mbar_wait_or_abort(&full[st], (uint32_t)(i / S) & 1u, abortp)) {
@@ -1287,11 +1292,17 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
                 cur = D.seg;
                 nrows = D.nrows;
                 nitems = nrows * r;
+                if constexpr (PAIR) {
+                    prow = tid % nrows;
+                    prhs0 = tid / nrows * 4;
+                    pcnt = tid < nrows * ((r + 3) / 4) ? min(4, r - prhs0) : 0;
+                } else {
 #pragma unroll
-                for (int j = 0; j < JM; ++j) {
-                    const int it = tid + kNearCons * j;
-                    irow[j] = it % nrows;
-                    icol[j] = it / nrows;
+                    for (int j = 0; j < JM; ++j) {
+                        const int it = tid + kNearCons * j;
+                        irow[j] = it % nrows;
+                        icol[j] = it / nrows;
+                    }
                 }
             }
             const unsigned char* stg = stage_base + (size_t)st * a.stage_bytes;
@@ -1299,15 +1310,26 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
             for (int p = 0; p < D.npieces; ++p) {
                 const SPiece P = spc[st][p];
                 if constexpr (PAIR) {
-                    const float2* A = reinterpret_cast<const float2*>(stg + P.smem_off);
-                    const float2* x = reinterpret_cast<const float2*>(xin + P.xoff);
+                    const float2* A = reinterpret_cast<const float2*>(stg + P.smem_off) + prow;
+                    const float2* x = reinterpret_cast<const float2*>(xin + P.xoff) + prhs0;
+                    if (pcnt == 4) {
 #pragma unroll 2
-                    for (int col = 0; col < P.ncols; ++col) {
-                        const float2* Ac = A + col * nrows;
-                        const float2* xc = x + col * r;
+                        for (int col = 0; col < P.ncols; ++col) {
+                            const float2 av = A[col * nrows];
+                            const float2* xc = x + col * r;
+                            pair_fma(av, xc[0], hi[0], lo[0]);
+                            pair_fma(av, xc[1], hi[1], lo[1]);
+                            pair_fma(av, xc[2], hi[2], lo[2]);
+                            pair_fma(av, xc[3], hi[3], lo[3]);
+                        }
+                    } else if (pcnt > 0) {
+                        for (int col = 0; col < P.ncols; ++col) {
+                            const float2 av = A[col * nrows];
+                            const float2* xc = x + col * r;
 #pragma unroll
-                        for (int j = 0; j < JM; ++j)
-                            if (tid + kNearCons * j < nitems) pair_fma(Ac[irow[j]], xc[icol[j]], hi[j], lo[j]);
+                            for (int j = 0; j < 4; ++j)
+                                if (j < pcnt) pair_fma(av, xc[j], hi[j], lo[j]);
+                        }
                     }
                 } else {
                     const double* A = reinterpret_cast<const double*>(stg + P.smem_off);
@@ -1326,9 +1348,14 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
             if (D.last) {
 #pragma unroll
                 for (int j = 0; j < JM; ++j) {
-                    const double v = PAIR ? (double)hi[j] + (double)lo[j] : acc[j];
-                    if (tid + kNearCons * j < nitems)
-                        atomicAdd(a.u2n + (int64_t)icol[j] * a.N + a.perm[D.out_row + irow[j]], v);
+                    if constexpr (PAIR) {
+                        if (j < pcnt)
+                            atomicAdd(a.u2n + (int64_t)(prhs0 + j) * a.N + a.perm[D.out_row + prow],
+                                      (double)hi[j] + (double)lo[j]);
+                    } else {
+                        if (tid + kNearCons * j < nitems)
+                            atomicAdd(a.u2n + (int64_t)icol[j] * a.N + a.perm[D.out_row + irow[j]], acc[j]);
+                    }
                     acc[j] = 0.0;
                     hi[j] = 0.0f;
                     lo[j] = 0.0f;
