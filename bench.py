@@ -43,7 +43,7 @@ PASS_NAMES = {0: "gather", 1: "up_leaf", 2: "up_transfer", 3: "coupling", 4: "do
 
 # fp32-onfly: FP32 far field with the coupling blocks evaluated in the product;
 # fp32-pair, bf16x3-pair: the near field of split-form products (r > 8) in
-# FP32 pairs with error-free products and sums (FP64-equivalent, ~1e-13)
+# FP32 pairs with error-free products and sums (FP64-equivalent, <= n * 2^-48 per row of n terms)
 PRECISIONS = ("fp64", "fp32", "tf32x3", "bf16x3", "fp32-onfly", "fp32-pair", "bf16x3-pair")
 DTYPES = {"fp64": "f64", "fp32": "f32+f64", "tf32x3": "tf32x3+f64", "bf16x3": "bf16x3+f64",
           "fp32-onfly": "f32+f64", "fp32-pair": "f32+f32x2+f64", "bf16x3-pair": "bf16x3+f32x2+f64"}

@@ -113,8 +113,9 @@ typedef enum { H2_COUPLING_STORED = 0, H2_COUPLING_ON_THE_FLY = 1 } h2_coupling;
  *   (Dekker 1971), the cross terms hi_a*lo_x + lo_a*hi_x, and a running sum
  *   kept as a rounded sum plus its TwoSum error (Knuth 1969).  Each leaf's
  *   result is converted to FP64 once and added to the FP64 output.  The
- *   relative error of one row's sum stays near 2^-48 times the sum of the
- *   magnitudes of its terms (about 1e-13 on the benchmark meshes), far inside
+ *   error of a row of n terms stays below n * 2^-48 times the sum of the
+ *   magnitudes of its terms (the low word's own rounding grows with the row;
+ *   about 6e-13 for 1000 terms), within the FP64 path's 1e-8 and far inside
  *   the reduced forms' 1e-5.  A paired copy of the near blocks is kept beside
  *   the FP64 ones (the same bytes again), which products with at most 8
  *   right-hand sides still use. */
@@ -240,6 +241,9 @@ typedef struct {
     int32_t precision, max_rhs;
     int32_t n_launches_matvec;     /* kernel launches per h2_matvec                     */
     int32_t n_passes;              /* block-sparse passes per h2_matvec                 */
+    int64_t bytes_near_pair;       /* device bytes of the paired near-field copy (0
+                                      unless h2_params.near_field = H2_NEAR_F32PAIR)   */
+    int32_t near_field, coupling;  /* h2_near_field and h2_coupling of the operator     */
 } h2_stats_t;
 
 int h2_stats(const h2_handle* op, h2_stats_t* out);

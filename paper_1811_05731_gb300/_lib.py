@@ -66,7 +66,8 @@ class Stats(ctypes.Structure):
                 ("macs_per_rhs", ctypes.c_int64), ("compression_ratio", ctypes.c_double),
                 ("assemble_seconds", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("max_rhs", ctypes.c_int32), ("n_launches_matvec", ctypes.c_int32),
-                ("n_passes", ctypes.c_int32)]
+                ("n_passes", ctypes.c_int32), ("bytes_near_pair", ctypes.c_int64),
+                ("near_field", ctypes.c_int32), ("coupling", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

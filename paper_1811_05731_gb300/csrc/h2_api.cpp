@@ -318,6 +318,9 @@ int h2_stats(const h2_handle* op, h2_stats_t* out) {
     out->max_rhs = op->params.max_rhs;
     out->n_launches_matvec = op->n_launches;
     out->n_passes = (int32_t)op->passes.size();
+    out->bytes_near_pair = op->d_near_pair ? op->near_hi - op->near_lo : 0;
+    out->near_field = op->params.near_field;
+    out->coupling = op->params.coupling;
     return H2_OK;
 }
 

@@ -121,3 +121,42 @@ def test_rejects_bad_indices_and_nulls(L):
     assert lib.h2_assemble(None, None, ctypes.byref(h)) == H2_ERR_INVALID_ARG
     assert lib.h2_matvec(None, None, None, 1, None) == H2_ERR_INVALID_ARG
     assert lib.h2_free(None) == 0
+
+
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a header struct, from a C program compiled here."""
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    body = "".join(f'    printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields)
+    src = ("#include <stddef.h>\n#include <stdio.h>\n#include \"h2bem.h\"\nint main(void) {\n"
+           f'    printf("%zu\\n", sizeof({struct}));\n{body}    return 0;\n}}\n')
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "layout.c")
+        exe = os.path.join(d, "layout")
+        with open(c, "w") as f:
+            f.write(src)
+        subprocess.run([cc, "-I", os.path.dirname(HEADER), c, "-o", exe], check=True, capture_output=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(v) for v in out[1:]]
+
+
+@pytest.mark.parametrize("struct,cls", [("h2_params", "Params"), ("h2_stats_t", "Stats"),
+                                        ("h2_tuning_t", "Tuning")])
+def test_binding_structs_match_the_header(struct, cls):
+    """The binding's ctypes structures have the header's size and field offsets."""
+    from paper_1811_05731_gb300 import _lib
+    C = getattr(_lib, cls)
+    names = [n for n, _ in C._fields_]
+    size, offs = _c_layout(struct, names)
+    assert ctypes.sizeof(C) == size
+    assert [getattr(C, n).offset for n in names] == offs
+
+
+def test_default_modes(L):
+    p = pkg.h2_default_params()
+    assert (p.schedule, p.autotune, p.coupling, p.near_field) == (pkg.SCHEDULE_FLOW, 0, pkg.COUPLING_STORED,
+                                                                  pkg.NEAR_FP64)

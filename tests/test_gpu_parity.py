@@ -333,6 +333,9 @@ def test_paired_near_field_within_budget(precision):
                       near_field=pkg.NEAR_F32PAIR)
     op64 = pkg.Operator(g, m=4, leaf=20, max_rhs=24, precision=PRECISIONS[precision])
     assert op.stats()["n_launches_matvec"] == 4 + 2
+    st, st64 = op.stats(), op64.stats()
+    assert (st["near_field"], st64["near_field"]) == (pkg.NEAR_F32PAIR, pkg.NEAR_FP64)
+    assert st["bytes_near_pair"] >= st["bytes_near"] > 0 and st64["bytes_near_pair"] == 0
     o = oracle.H2Oracle(m.xyz, m.tri, 4, 20, 2.0)
     for r in (24, 17, 9, 3):
         x = _inputs(m, r, seed=17)
