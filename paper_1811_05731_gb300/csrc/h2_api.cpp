@@ -12,6 +12,11 @@
 namespace h2 {
 static thread_local std::string g_last_error;
 void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+void set_cuda_error(cudaError_t e, const char* call, const char* file, int line) {
+    const char* base = std::strrchr(file, '/');
+    g_last_error = std::string(cudaGetErrorString(e)) + " (" + (base ? base + 1 : file) + ":" +
+                   std::to_string(line) + ": " + call + ")";
+}
 }  // namespace h2
 
 namespace {

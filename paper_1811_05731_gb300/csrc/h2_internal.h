@@ -339,15 +339,18 @@ void drop_batch_plans(uint64_t serial);   // forget the plans that use an operat
 int autotune(h2_handle* op, int r, cudaStream_t s, h2_tuning_t* out);
 }  // namespace h2
 
+// Returns H2_ERR_OOM or H2_ERR_CUDA from the enclosing function when a CUDA
+// call fails; the message names the error, the call and its source line.
 #define H2_CUDA_TRY(call)                                        \
     do {                                                         \
         cudaError_t e_ = (call);                                 \
         if (e_ != cudaSuccess) {                                 \
-            h2::set_last_error(cudaGetErrorString(e_));          \
+            h2::set_cuda_error(e_, #call, __FILE__, __LINE__);   \
             return e_ == cudaErrorMemoryAllocation ? H2_ERR_OOM : H2_ERR_CUDA; \
         }                                                        \
     } while (0)
 
 namespace h2 {
 void set_last_error(const char* msg);
+void set_cuda_error(cudaError_t e, const char* call, const char* file, int line);
 }

@@ -2089,6 +2089,26 @@ int matvec_device(h2_handle* op, const double* u1, double* u2, int r, cudaStream
     return launch_matvec(op, u1, u2, r, s, op->d_ws, op->d_ws32, op->use_flow != 0, nullptr, nullptr);
 }
 
+// The largest dynamic shared memory one segment-kernel CTA can be given: the
+// device's per-block opt-in limit less the kernel's static shared memory (the
+// same for every instantiation).
+static size_t seg_smem_max() {
+    static size_t v = 0;
+    if (v == 0) {
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa{};
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+            cudaFuncGetAttributes(&fa, k_seg<32, true, true>) == cudaSuccess && optin > (int)fa.sharedSizeBytes) {
+            v = (size_t)optin - fa.sharedSizeBytes;
+        } else {
+            cudaGetLastError();
+            v = (size_t)220 * 1024;
+        }
+    }
+    return v;
+}
+
 // Times one configuration: `iters` products after two unmeasured ones.
 static int time_products(h2_handle* op, const double* x, double* y, int r, cudaStream_t s, int iters,
                          double* ms) {
@@ -2146,7 +2166,7 @@ int autotune(h2_handle* op, int r, cudaStream_t s, h2_tuning_t* out) {
         for (int stages = 2; stages <= 4 && rc == H2_OK; ++stages) {
             op->tune_stages = stages;
             const size_t smem = pass_smem_bytes(op, rt);
-            if (smem > (size_t)227 * 1024) continue;
+            if (smem > seg_smem_max()) continue;
             int occ = 1;
             switch (rt) {
                 case 1: occ = tc ? seg_occupancy<1, true>(smem) : seg_occupancy<1, false>(smem); break;
@@ -2192,14 +2212,25 @@ int autotune(h2_handle* op, int r, cudaStream_t s, h2_tuning_t* out) {
     if (rc == H2_OK && (prec == H2_TF32X3 || prec == H2_BF16X3) && rt <= kTcCudaMaxRT) {
         const int cur = op->tc_small_r_cuda;
         op->use_flow = best_flow;
-        op->tune_stages = best_st;
         op->tune_ctas = best_ct;
         op->tc_small_r_cuda = !cur;
+        // the other pipe with the best stage count, or fewer stages where its
+        // operand buffers (tensor-core tiles) no longer fit beside that many
+        int st = best_st;
+        op->tune_stages = st;
+        while (st > 2 && pass_smem_bytes(op, rt) > seg_smem_max()) op->tune_stages = --st;
         double ms = 0.0;
-        rc = time_products(op, x, y, r, s, iters, &ms);
-        ++ncand;
-        if (rc == H2_OK && ms < best) best = ms;
-        else op->tc_small_r_cuda = cur;
+        const bool fits = pass_smem_bytes(op, rt) <= seg_smem_max();
+        if (fits) {
+            rc = time_products(op, x, y, r, s, iters, &ms);
+            ++ncand;
+        }
+        if (fits && rc == H2_OK && ms < best) {
+            best = ms;
+            best_st = st;
+        } else {
+            op->tc_small_r_cuda = cur;
+        }
     }
     op->use_flow = best_flow;
     op->tune_stages = best_st;
