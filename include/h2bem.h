@@ -118,7 +118,10 @@ typedef enum { H2_COUPLING_STORED = 0, H2_COUPLING_ON_THE_FLY = 1 } h2_coupling;
  *   about 6e-13 for 1000 terms), within the FP64 path's 1e-8 and far inside
  *   the reduced forms' 1e-5.  A paired copy of the near blocks is kept beside
  *   the FP64 ones (the same bytes again), which products with at most 8
- *   right-hand sides still use. */
+ *   right-hand sides still use.  An operator without the split form (a leaf
+ *   above 64 rows, or the level-wise schedule without h2_params.autotune)
+ *   keeps the FP64 near field for every product; h2_stats reports
+ *   bytes_near_pair = 0 then. */
 typedef enum { H2_NEAR_FP64 = 0, H2_NEAR_F32PAIR = 1 } h2_near_field;
 
 /* H2_SCHEDULE_FLOW (default): one persistent kernel after the input gather;
