@@ -149,6 +149,30 @@ def ellipsoid(level: int, axes=(3.0, 2.0, 1.0)) -> Mesh:
     return Mesh(xyz, m.tri, f"ellipsoid{level}").contiguous()
 
 
+def torus_surface(nu: int, nv: int, R: float = 2.0, r: float = 1.0) -> Mesh:
+    """Torus of revolution about z (centre-line radius R, tube radius r; the
+    default aspect ratio R : r = 2 : 1), an nu x nv grid in the angles u about
+    z and v about the tube, each quad split into two triangles.  Genus 1, so
+    it has saddle-shaped (non-convex) vertex fans on the inner side.
+    Nodes: nu nv."""
+    u = 2.0 * np.pi * np.arange(nu) / nu
+    v = 2.0 * np.pi * np.arange(nv) / nv
+    U, V = np.meshgrid(u, v, indexing="ij")
+    A = R + r * np.cos(V)
+    xyz = np.stack([A * np.cos(U), A * np.sin(U), r * np.sin(V)], axis=-1).reshape(-1, 3)
+
+    def node(i, j):
+        return (i % nu) * nv + (j % nv)
+
+    tris = []
+    for i in range(nu):
+        for j in range(nv):
+            # d/du x d/dv points away from the tube's centre line (outward)
+            p00, p10, p11, p01 = node(i, j), node(i + 1, j), node(i + 1, j + 1), node(i, j + 1)
+            tris += [[p00, p10, p11], [p00, p11, p01]]
+    return Mesh(xyz, np.asarray(tris, dtype=np.int32), f"torus{nu}x{nv}").contiguous()
+
+
 def transformed(mesh: Mesh, rot: np.ndarray, shift, scale: float) -> Mesh:
     """Rigid motion plus uniform scaling x -> scale * rot @ x + shift (rot proper, det +1)."""
     xyz = scale * (mesh.xyz @ np.asarray(rot, dtype=np.float64).T) + np.asarray(shift)[None, :]

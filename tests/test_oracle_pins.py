@@ -201,6 +201,73 @@ def test_cube_demag_factor_symmetry_and_convergence():
     assert errs[1] < errs[0] and errs[2] < errs[1] and errs[2] < 5e-3, errs
 
 
+def aharoni_nz(a, b, c):
+    """Demagnetising factor along z of the homogeneously magnetised prism
+    |x| <= a, |y| <= b, |z| <= c (Aharoni, J. Appl. Phys. 83, 3432 (1998),
+    Eq. 1; the paper's Section "Rectangular prism" compares against it).  The
+    closed form is pinned below by the cube value and the trace identity."""
+    d = math.sqrt(a * a + b * b + c * c)
+    ab, bc, ac = math.hypot(a, b), math.hypot(b, c), math.hypot(a, c)
+    s = ((b * b - c * c) / (2 * b * c) * math.log((d - a) / (d + a))
+         + (a * a - c * c) / (2 * a * c) * math.log((d - b) / (d + b))
+         + b / (2 * c) * math.log((ab + a) / (ab - a))
+         + a / (2 * c) * math.log((ab + b) / (ab - b))
+         + c / (2 * a) * math.log((bc - b) / (bc + b))
+         + c / (2 * b) * math.log((ac - a) / (ac + a))
+         + 2 * math.atan(a * b / (c * d))
+         + (a ** 3 + b ** 3 - 2 * c ** 3) / (3 * a * b * c)
+         + (a * a + b * b - 2 * c * c) / (3 * a * b * c) * d
+         + c / (a * b) * (ac + bc)
+         - (ab ** 3 + bc ** 3 + ac ** 3) / (3 * a * b * c))
+    return s / math.pi
+
+
+def test_aharoni_prism_factors_pinned():
+    """The closed form reproduces the cube's 1/3, the trace N_x + N_y + N_z = 1
+    of the demagnetising tensor for unequal sides, and the thin-plate (N -> 1)
+    and long-rod (N -> 0) limits along the short and the long axis."""
+    assert abs(aharoni_nz(1.0, 1.0, 1.0) - GOLDEN["cube_demag_factor"]["value"]) < 1e-14
+    for a, b, c in ((5.0, 10.0, 0.5), (1.0, 2.0, 3.0), (0.3, 7.0, 2.0)):
+        tr = aharoni_nz(a, b, c) + aharoni_nz(b, c, a) + aharoni_nz(c, a, b)
+        assert abs(tr - 1.0) < 1e-12, (a, b, c, tr)
+    thin = [1.0 - aharoni_nz(1.0, 1.0, c) for c in (1e-2, 1e-3, 1e-4, 1e-5)]
+    rod = [aharoni_nz(1.0, 1.0, c) for c in (1e2, 1e3, 1e4)]
+    assert all(q < p / 5 for p, q in zip(thin, thin[1:])) and thin[-1] < 1e-4, thin
+    assert all(q < p / 5 for p, q in zip(rod, rod[1:])) and rod[-1] < 1e-4, rod
+
+
+def test_prism_10_20_1_demag_factor_converges_to_aharoni():
+    """Section "Rectangular prism": the 10:20:1 prism magnetised out of plane
+    (along the short axis).  u1 = z solves the Neumann problem exactly on the
+    polyhedron, u2 = M u1 on the boundary, and the boundary form of the energy
+    gives N_z; it converges to Aharoni's value under refinement (slower than on
+    the sphere, as the paper observes for the prism: the field is singular at
+    edges and corners)."""
+    target = aharoni_nz(5.0, 10.0, 0.5)
+    errs = []
+    for k in (1, 2, 4):
+        m = synth.box_surface(10 * k, 20 * k, k, 10.0, 20.0, 1.0)
+        u1 = m.xyz[:, 2].copy()
+        u2 = oracle.dense_matvec(m.xyz, m.tri, u1[None, :])[0]
+        errs.append(abs(oracle.demag_factor(m.xyz, m.tri, u1 + u2, (0.0, 0.0, 1.0)) - target) / target)
+    assert errs[1] < errs[0] / 2.5 and errs[2] < errs[1] / 2.5, errs
+    assert errs[2] < 3e-3, errs
+
+
+def test_torus_gauss_identity_and_zero_energy():
+    """Section "Torus": a 2:1 torus of revolution (genus 1, saddle-shaped vertex
+    fans on its inner side) magnetised azimuthally has no volume or surface
+    charge, so u1 is constant and the energy is zero.  On the discrete operator
+    that is Gauss's identity M 1 = -1 at every node, which holds to rounding
+    here as on convex surfaces: u = u1 + M u1 vanishes and so does e_d."""
+    for nu, nv in (24, 12), (48, 24):
+        m = synth.torus_surface(nu, nv)
+        y = oracle.dense_matvec(m.xyz, m.tri, np.ones((1, m.n_vertices)))[0]
+        assert np.max(np.abs(y - GOLDEN["constant_u1_response"]["value"])) < 1e-13
+        u = 1.0 + y
+        assert abs(oracle.demag_factor(m.xyz, m.tri, u, (1.0, 0.0, 0.0))) < 1e-13
+
+
 def test_rigid_motion_and_scale_invariance():
     m = synth.icosphere(2)
     M = oracle.dense_matrix(m.xyz, m.tri)

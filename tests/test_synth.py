@@ -54,3 +54,21 @@ def test_eight_uneven_meshes():
     sizes = [m.n_vertices for m in ms]
     assert len(ms) == 8 and sum(sizes) == 266742
     assert min(sizes) >= 5000 and max(sizes) <= 100000
+
+
+def test_torus_is_a_closed_outward_genus_one_surface():
+    """The torus used for the zero-energy pin: V - E + F = 0 (genus 1), every
+    edge in two triangles, each directed edge once (consistent orientation),
+    and an enclosed volume that converges to 2 pi^2 R r^2 from below."""
+    vols = []
+    for nu, nv in ((24, 12), (48, 24), (96, 48)):
+        m = synth.torus_surface(nu, nv)
+        e = _edges(m.tri)
+        assert m.n_vertices - len(e) + m.n_triangles == 0
+        assert 2 * len(e) == 3 * m.n_triangles
+        d = np.concatenate([m.tri[:, [0, 1]], m.tri[:, [1, 2]], m.tri[:, [2, 0]]])
+        assert len(np.unique(d, axis=0)) == len(d)
+        vols.append(oracle.enclosed_volume(m.xyz, m.tri))
+    exact = 2.0 * np.pi ** 2 * 2.0 * 1.0
+    assert 0.0 < vols[0] < vols[1] < vols[2] < exact
+    assert (exact - vols[2]) / exact < 5e-3
