@@ -1114,7 +1114,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
 // first: a segment, or a run of its chunks where a few SMs would otherwise
 // finish the largest leaves alone; a unit's sums are added to the cleared
 // u2n (a value receives one addition per unit of its leaf).  No unit waits
-// for another.
+// for another.  The paired form (PAIR, h2_near_field H2_NEAR_F32PAIR) stages
+// the paired copy of the blocks and the paired inputs (8 bytes per value as
+// in FP64) and gives each thread one output row and four consecutive
+// right-hand sides instead, so that one entry load serves four products.
 // ---------------------------------------------------------------------------
 constexpr int kNearCons = 256;
 constexpr int kNearBlock = kNearCons + 32;
