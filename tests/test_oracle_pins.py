@@ -279,6 +279,61 @@ def test_rigid_motion_and_scale_invariance():
     assert np.max(np.abs(M - M2)) < 1e-12
 
 
+def _rotation(q):
+    """Rotation matrix of the (not necessarily unit) quaternion q."""
+    w, a, b, c = np.asarray(q, dtype=np.float64) / np.linalg.norm(q)
+    return np.array([[1 - 2 * (b * b + c * c), 2 * (a * b - c * w), 2 * (a * c + b * w)],
+                     [2 * (a * b + c * w), 1 - 2 * (a * a + c * c), 2 * (b * c - a * w)],
+                     [2 * (a * c - b * w), 2 * (b * c + a * w), 1 - 2 * (a * a + b * b)]])
+
+
+def test_property_rigid_motion_scale_and_gauss():
+    """Property test: for random rotations, translations and scales over six
+    decades, the double-layer operator is unchanged (it is dimensionless and
+    depends only on relative positions) and Gauss's identity M 1 = -1 holds."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+    m = synth.icosphere(1)
+    M = oracle.dense_matrix(m.xyz, m.tri)
+
+    @hyp.settings(max_examples=30, deadline=None, derandomize=True)
+    @hyp.given(q=st.lists(st.floats(-1, 1), min_size=4, max_size=4).filter(lambda v: np.linalg.norm(v) > 0.1),
+               t=st.lists(st.floats(-100, 100), min_size=3, max_size=3),
+               logs=st.floats(-3, 3))
+    def check(q, t, logs):
+        m2 = synth.transformed(m, _rotation(q), t, 10.0 ** logs)
+        M2 = oracle.dense_matrix(m2.xyz, m2.tri)
+        # positions far from the origin relative to the mesh lose digits in x - y
+        tol = 1e-12 * max(1.0, np.max(np.abs(t)) / 10.0 ** logs)
+        assert np.max(np.abs(M2 - M)) < tol
+        assert np.max(np.abs(M2.sum(axis=1) + 1.0)) < tol
+
+    check()
+
+
+def test_h2_oracle_is_translation_and_scale_invariant():
+    """Scalings by powers of two and small dyadic translations move the boxes,
+    the Chebyshev nodes and the kernel together and keep every coordinate
+    comparison of the tree build (nodes lying exactly on a split plane), so the
+    tree is the same and the H2 product of the moved mesh equals the original
+    to rounding, although S, V and W individually scale.  (A translation that
+    rounds the coordinates can move such a node across a split plane: a
+    different tree, and a product that differs at the level of the H2 error.)"""
+    m = synth.icosphere(3)
+    x = synth.gaussian_rhs(m.n_vertices, 2, 4)
+    h = oracle.H2Oracle(m.xyz, m.tri, 3, 32, 2.0)
+    y = h.matvec(x)
+    t = h.tree()
+    for shift, scale in (([0.0, 0.0, 0.0], 2.0 ** -10), ([0.0, 0.0, 0.0], 2.0 ** 8),
+                         ([0.5, -0.25, 0.125], 1.0)):
+        m2 = synth.transformed(m, np.eye(3), shift, scale)
+        h2 = oracle.H2Oracle(m2.xyz, m2.tri, 3, 32, 2.0)
+        t2 = h2.tree()
+        assert all(np.array_equal(t[k], t2[k]) for k in t if k != "box"), (shift, scale)
+        y2 = h2.matvec(x)
+        assert np.max(np.abs(y2 - y)) < 1e-12 * np.max(np.abs(y)), (shift, scale)
+
+
 # ---------------------------------------------------------------- H2 pieces
 def test_gauss_legendre_matches_numpy():
     for q in (1, 2, 4, 7, 12):
