@@ -16,6 +16,9 @@ Equation names refer to arXiv:1811.05731.
   Chebyshev-interpolation H2 product (Section "H2-Matrix Compression").
 * ``demag_factor``: e_d / K_d from boundary values of u = u1 + u2 for a
   uniform magnetisation (Section "Sphere": e_d = mu0 N Ms^2 / 2).
+* ``recompress`` (module, numpy): algebraic recompression of the H2 far field
+  (orthogonalised nested bases truncated with total cluster-basis weights),
+  the reference for a recompressed product.
 """
 from __future__ import annotations
 
