@@ -19,6 +19,9 @@ Equation names refer to arXiv:1811.05731.
 * ``recompress`` (module, numpy): algebraic recompression of the H2 far field
   (orthogonalised nested bases truncated with total cluster-basis weights),
   the reference for a recompressed product.
+* ``fem`` (module, numpy / scipy.sparse): the full FEM/BEM pipeline on small
+  tetrahedral meshes (P1 Neumann solve for u1, u2 on the boundary through the
+  dense operator, P1 Dirichlet solve, volume energy).
 """
 from __future__ import annotations
 

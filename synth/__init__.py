@@ -2,7 +2,8 @@
 
 This package is shared by the CPU oracle, the tests and the benchmark. It holds
 none of the boundary-operator arithmetic: only mesh generators (icosphere, box
-surfaces, mapped spheres, ellipsoids, tori) and seeded vectors u1 at the nodes.
+surfaces, mapped spheres, ellipsoids, tori), tetrahedral volume meshes of a
+cube and a ball (``synth.volume``) and seeded vectors u1 at the nodes.
 """
 from .meshes import (  # noqa: F401
     Mesh, icosphere, box_surface, cube_surface, cube_sphere, ellipsoid, film_box, torus_surface,

@@ -72,3 +72,23 @@ def test_torus_is_a_closed_outward_genus_one_surface():
     exact = 2.0 * np.pi ** 2 * 2.0 * 1.0
     assert 0.0 < vols[0] < vols[1] < vols[2] < exact
     assert (exact - vols[2]) / exact < 5e-3
+
+
+@pytest.mark.parametrize("which,n", [("cube", 4), ("ball", 6)])
+def test_volume_meshes_and_their_boundaries(which, n):
+    """Tetrahedral meshes of the full-pipeline checks: every tetrahedron
+    positively oriented, volumes summing to the body's, and a boundary that is
+    a closed genus-0 surface, outward, enclosing the same volume."""
+    from synth import volume as vm
+    xyz, tets = vm.cube_tets(n) if which == "cube" else vm.ball_tets(n)
+    p = xyz[tets]
+    vol = np.einsum("ij,ij->i", p[:, 1] - p[:, 0], np.cross(p[:, 2] - p[:, 0], p[:, 3] - p[:, 0])) / 6.0
+    assert np.all(vol > 0)
+    surf, nodes = vm.boundary_surface(xyz, tets)
+    e = _edges(surf.tri)
+    assert surf.n_vertices - len(e) + surf.n_triangles == 2 and 2 * len(e) == 3 * surf.n_triangles
+    assert abs(oracle.enclosed_volume(surf.xyz, surf.tri) - vol.sum()) < 1e-12 * vol.sum()
+    if which == "cube":
+        assert abs(vol.sum() - 1.0) < 1e-12
+    else:
+        assert np.allclose(np.linalg.norm(surf.xyz, axis=1), 1.0)
