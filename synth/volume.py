@@ -6,6 +6,8 @@
   permutation of the axes.
 * ``ball_tets``: the same grid on [-1, 1]^3 mapped radially onto the unit
   ball (x -> x |x|_inf / |x|_2), which sends the cube's surface onto the sphere.
+* ``torus_tets``: a solid torus of revolution, the same split of a
+  (tube disc x angle) grid.
 * ``boundary_surface``: the faces that belong to one tetrahedron only, oriented
   outward, as a surface ``Mesh`` plus the volume index of every surface node.
 
@@ -67,6 +69,38 @@ def ball_tets(n: int):
     scale = np.where(r2 > 0, rinf / np.where(r2 > 0, r2, 1.0), 0.0)
     xyz = xyz * scale[:, None]
     return xyz, _orient(xyz, _kuhn_tets(n))
+
+
+def torus_tets(nu: int, nc: int, R: float = 2.0, r: float = 1.0):
+    """(xyz, tets) of the solid torus of revolution about z (centre-line radius
+    R, tube radius r): an nc x nc grid on [-1, 1]^2 mapped radially onto the
+    tube's disc, swept over nu angles about z (periodic), each cell of the
+    (disc, angle) grid split into six tetrahedra like ``cube_tets``."""
+    g = np.linspace(-1.0, 1.0, nc + 1)
+    A, B = np.meshgrid(g, g, indexing="ij")
+    ab = np.stack([A.ravel(), B.ravel()], axis=1)
+    r2 = np.linalg.norm(ab, axis=1)
+    rinf = np.max(np.abs(ab), axis=1)
+    ab = ab * np.where(r2 > 0, rinf / np.where(r2 > 0, r2, 1.0), 0.0)[:, None]
+    u = 2.0 * np.pi * np.arange(nu) / nu
+    rho = R + r * ab[:, 0]
+    xyz = np.stack([np.outer(np.cos(u), rho), np.outer(np.sin(u), rho),
+                    np.broadcast_to(r * ab[:, 1], (nu, ab.shape[0]))], axis=-1).reshape(-1, 3)
+    m = nc + 1
+
+    def vid(i, j, k):
+        return (k % nu) * m * m + i * m + j
+
+    tets = []
+    for i, j, k in itertools.product(range(nc), range(nc), range(nu)):
+        for perm in itertools.permutations(range(3)):
+            p = [i, j, k]
+            verts = [vid(*p)]
+            for ax in perm:
+                p[ax] += 1
+                verts.append(vid(*p))
+            tets.append(verts)
+    return xyz, _orient(xyz, np.asarray(tets, dtype=np.int64))
 
 
 def boundary_surface(xyz: np.ndarray, tets: np.ndarray):

@@ -60,3 +60,26 @@ def test_ball_factor_converges_at_second_order_and_u2_inside():
         u2errs.append(np.max(np.abs(u2[inner] - (u2[inner].mean() - 2.0 / 3.0 * (xyz[inner, 2] - xyz[inner, 2].mean())))))
     assert errs[1] < errs[0] / 3.5 and errs[1] < 4e-3, errs
     assert u2errs[1] < u2errs[0] and u2errs[1] < 2e-2, u2errs
+
+
+def test_torus_azimuthal_energy_vanishes():
+    """Section "Torus": a 2:1 solid torus magnetised azimuthally has neither
+    volume nor surface charges, so e_d = 0.  With M piecewise constant (the
+    azimuthal direction at each tetrahedron's centroid) the computed energy is
+    a discretisation error that falls quickly under refinement, while a uniform
+    M on the same meshes gives an O(1) energy."""
+    es = []
+    for nu, nc in ((12, 2), (24, 4), (36, 6)):
+        xyz, tets = vm.torus_tets(nu, nc)
+        surf, nodes = vm.boundary_surface(xyz, tets)
+        e_tri = np.unique(np.sort(np.concatenate([surf.tri[:, [0, 1]], surf.tri[:, [1, 2]], surf.tri[:, [2, 0]]]),
+                                  axis=1), axis=0)
+        assert surf.n_vertices - len(e_tri) + surf.n_triangles == 0   # genus 1
+        c = xyz[tets].mean(axis=1)
+        phi = np.arctan2(c[:, 1], c[:, 0])
+        M = np.stack([-np.sin(phi), np.cos(phi), np.zeros_like(phi)], axis=1)
+        es.append(abs(fem.pipeline(xyz, tets, M, surf, nodes)[-1]))
+        if nc == 4:
+            ez = fem.pipeline(xyz, tets, np.array([0.0, 0.0, 1.0]), surf, nodes)[-1]
+            assert 0.3 < ez < 0.7
+    assert es[1] < es[0] / 5 and es[2] < es[1] / 3 and es[2] < 1e-6, es
