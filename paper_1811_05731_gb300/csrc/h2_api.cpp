@@ -7,6 +7,8 @@
 #include <new>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "h2_internal.h"
 
 namespace h2 {
@@ -20,6 +22,15 @@ void set_cuda_error(cudaError_t e, const char* call, const char* file, int line)
 }  // namespace h2
 
 namespace {
+
+// One NVTX range per public call (a no-op unless a profiler is attached), so
+// that a timeline shows assembly, tuning and every product by name.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 void free_device(h2_handle* h) {
     auto f = [](void* p) {
@@ -125,6 +136,7 @@ int h2_build_geometry(const double* xyz, int64_t n_vertices, const int32_t* tri,
 }
 
 int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_op) {
+    const Range range("h2_assemble");
     if (!geom_c || !out_op) return H2_ERR_INVALID_ARG;
     *out_op = nullptr;
     if (geom_c->kind != 1) return H2_ERR_WRONG_HANDLE;
@@ -206,6 +218,7 @@ int h2_fault_inject_stall(h2_handle* op, int32_t enable) {
 }
 
 int h2_autotune(h2_handle* op, int32_t r, void* cuda_stream, h2_tuning_t* out) {
+    const Range range("h2_autotune");
     if (!op) return H2_ERR_INVALID_ARG;
     if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
     if (r < 1 || r > op->params.max_rhs) return H2_ERR_INVALID_ARG;
@@ -213,6 +226,7 @@ int h2_autotune(h2_handle* op, int32_t r, void* cuda_stream, h2_tuning_t* out) {
 }
 
 int h2_matvec(h2_handle* op, const double* u1, double* u2, int32_t r, void* cuda_stream) {
+    const Range range("h2_matvec");
     if (!op || !u1 || !u2) return H2_ERR_INVALID_ARG;
     if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
     if (r < 1) return H2_ERR_INVALID_ARG;
@@ -377,6 +391,7 @@ int h2_free(h2_handle* h) {
 
 int h2_matvec_batched(h2_handle* const* ops, int32_t n_ops, const double* const* u1, double* const* u2,
                       const int32_t* r, void* cuda_stream) {
+    const Range range("h2_matvec_batched");
     if (!ops || !u1 || !u2 || !r || n_ops < 1 || n_ops > H2_MAX_BATCH) return H2_ERR_INVALID_ARG;
     for (int i = 0; i < n_ops; ++i) {
         if (!ops[i] || !u1[i] || !u2[i]) return H2_ERR_INVALID_ARG;
