@@ -55,7 +55,8 @@ typedef enum {
 
 /* Storage/arithmetic precision of the far field (transfer, coupling and leaf
  * bases).  Near blocks, the solid-angle diagonal, the geometry and the final
- * per-node sum are FP64 in every mode.
+ * per-node sum are FP64 in every mode (the near field's arithmetic has one
+ * FP64-equivalent alternative, h2_params.near_field).
  *  H2_FP64:   everything FP64 (CUDA cores).
  *  H2_FP32:   far-field matrices and vectors (x-hat, y-hat) in FP32, FP32
  *             products with FP32 accumulation on the CUDA cores.
