@@ -304,6 +304,34 @@ int h2_profile_read(h2_handle* op, int32_t capacity, int32_t* kind, double* ms_t
                     int64_t* bytes, int64_t* macs, int32_t* grid, int32_t* n_calls,
                     int32_t* n_entries);
 
+/* Host-only check of the execution plan (no device work, usable without a
+ * GPU): builds, for a mesh and parameters, the cluster tree, the block
+ * partition (Section "H2-Matrix Compression"), the passes of the product and
+ * the dataflow ticket order (with and without the near field) exactly as
+ * h2_assemble does, with the ticket order simulated for `workers` concurrent
+ * CTAs, and checks the invariants the product kernels rely on, independently
+ * of the code that built them: every chunk a legal bulk copy (16-byte aligned
+ * source and size, within one stage, input rows on 4-row boundaries, one
+ * piece type per chunk, one accumulator kind per segment); the ticket order
+ * topological (every producer of a region a segment waits for holds an
+ * earlier ticket, so persistent CTAs cannot deadlock); every region's
+ * expected signal count equal to the writer signals of its producers.
+ * `violations` counts the failed checks (0 for a sound plan).  The mesh is
+ * validated as by h2_build_geometry (same error codes); `params` as by
+ * h2_assemble (NULL: defaults).  Host arrays only. */
+typedef struct {
+    int32_t n_clusters, n_levels;
+    int64_t n_far_blocks, n_near_blocks;
+    int64_t n_segments, n_chunks;     /* dataflow form with the near field        */
+    int64_t n_split_segments;         /* without the near field (-1: no order)     */
+    int32_t n_regions, violations;
+    int64_t bytes_streamed;           /* matrix bytes one product reads            */
+    double makespan_us;               /* simulated makespan of the ticket order    */
+} h2_plan_report_t;
+
+int h2_plan_check(const double* xyz, int64_t n_vertices, const int32_t* tri, int64_t n_triangles,
+                  const h2_params* params, int32_t workers, h2_plan_report_t* out);
+
 /* Release a geometry or operator handle; NULL is a no-op.  Releasing a handle
  * twice is undefined. */
 int h2_free(h2_handle* h);

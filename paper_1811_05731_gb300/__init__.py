@@ -19,7 +19,7 @@ from ._lib import (  # noqa: F401
     H2Error, Params, Stats, FP64, FP32, TF32X3, BF16X3, matvec_batched, h2_matvec_batched, h2_autotune, SCHEDULE_FLOW, SCHEDULE_LEVELS,
     COUPLING_STORED, COUPLING_ON_THE_FLY, NEAR_FP64, NEAR_F32PAIR, lib, load,
     h2_default_params, h2_build_geometry, h2_assemble, h2_matvec, h2_matvec_noalloc, h2_free,
-    h2_stats,
+    h2_stats, h2_plan_check, PlanReport,
     h2_get_tree, h2_get_blocks, h2_get_psi, h2_device_status, h2_error_string,
     Geometry, Operator,
 )

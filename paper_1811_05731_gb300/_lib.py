@@ -47,6 +47,18 @@ class Params(ctypes.Structure):
                 ("autotune", ctypes.c_int32), ("coupling", ctypes.c_int32), ("near_field", ctypes.c_int32)]
 
 
+class PlanReport(ctypes.Structure):
+    _fields_ = [("n_clusters", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("n_far_blocks", ctypes.c_int64), ("n_near_blocks", ctypes.c_int64),
+                ("n_segments", ctypes.c_int64), ("n_chunks", ctypes.c_int64),
+                ("n_split_segments", ctypes.c_int64), ("n_regions", ctypes.c_int32),
+                ("violations", ctypes.c_int32), ("bytes_streamed", ctypes.c_int64),
+                ("makespan_us", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("stages", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("n_candidates", ctypes.c_int32), ("ms_best", ctypes.c_double), ("ms_default", ctypes.c_double)]
@@ -104,10 +116,12 @@ def load(path: str | None = None):
         L.h2_get_psi.argtypes = [_vp, _c_d]
         L.h2_device_status.argtypes = [_vp]
         L.h2_free.argtypes = [_vp]
+        L.h2_plan_check.argtypes = [_c_d, ctypes.c_int64, _c_i32, ctypes.c_int64, ctypes.POINTER(Params),
+                                    ctypes.c_int32, ctypes.POINTER(PlanReport)]
         for f in ("h2_build_geometry", "h2_assemble", "h2_matvec", "h2_matvec_noalloc", "h2_matvec_batched",
                   "h2_autotune", "h2_fault_inject_stall",
                   "h2_stats", "h2_get_tree",
-                  "h2_get_blocks", "h2_get_psi", "h2_device_status", "h2_free"):
+                  "h2_get_blocks", "h2_get_psi", "h2_device_status", "h2_free", "h2_plan_check"):
             getattr(L, f).restype = ctypes.c_int
         _LIB = L
         return L
@@ -198,6 +212,18 @@ def matvec_batched(operators, xs, ys=None, stream=None):
     h2_matvec_batched([o.handle for o in operators], [x.data_ptr() for x in xs], [y.data_ptr() for y in ys],
                       [x.shape[0] for x in xs], stream)
     return ys
+
+
+def h2_plan_check(xyz, tri, workers: int = 456, **params) -> dict:
+    """Host-only build and check of the execution plan (no GPU needed); see
+    h2_plan_check in h2bem.h.  ``params`` as for :func:`h2_default_params`."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    p = h2_default_params(**params)
+    rep = PlanReport()
+    _check(lib().h2_plan_check(xyz.ctypes.data_as(_c_d), xyz.shape[0], tri.ctypes.data_as(_c_i32), tri.shape[0],
+                               ctypes.byref(p), int(workers), ctypes.byref(rep)), "h2_plan_check")
+    return rep.as_dict()
 
 
 def h2_stats(op: int) -> dict:
