@@ -327,6 +327,7 @@ typedef struct {
     int32_t n_regions, violations;
     int64_t bytes_streamed;           /* matrix bytes one product reads            */
     double makespan_us;               /* simulated makespan of the ticket order    */
+    double split_makespan_us;         /* the same without the near field (-1)      */
 } h2_plan_report_t;
 
 int h2_plan_check(const double* xyz, int64_t n_vertices, const int32_t* tri, int64_t n_triangles,

@@ -53,7 +53,7 @@ class PlanReport(ctypes.Structure):
                 ("n_segments", ctypes.c_int64), ("n_chunks", ctypes.c_int64),
                 ("n_split_segments", ctypes.c_int64), ("n_regions", ctypes.c_int32),
                 ("violations", ctypes.c_int32), ("bytes_streamed", ctypes.c_int64),
-                ("makespan_us", ctypes.c_double)]
+                ("makespan_us", ctypes.c_double), ("split_makespan_us", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

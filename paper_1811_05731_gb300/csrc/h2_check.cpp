@@ -149,6 +149,7 @@ int h2_plan_check(const double* xyz, int64_t n_vertices, const int32_t* tri, int
         out->n_chunks = (int64_t)full.chunk.size();
         out->n_regions = full.nreg;
         out->n_split_segments = ms_split >= 0.0 ? (int64_t)split.seg.size() : -1;
+        out->split_makespan_us = ms_split;
         out->bytes_streamed = op->bytes_streamed;
         out->violations = bad;
     }

@@ -145,7 +145,7 @@ def _c_layout(struct, fields):
 
 
 @pytest.mark.parametrize("struct,cls", [("h2_params", "Params"), ("h2_stats_t", "Stats"),
-                                        ("h2_tuning_t", "Tuning")])
+                                        ("h2_tuning_t", "Tuning"), ("h2_plan_report_t", "PlanReport")])
 def test_binding_structs_match_the_header(struct, cls):
     """The binding's ctypes structures have the header's size and field offsets."""
     from paper_1811_05731_gb300 import _lib
