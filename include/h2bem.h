@@ -307,8 +307,9 @@ int h2_profile_read(h2_handle* op, int32_t capacity, int32_t* kind, double* ms_t
 /* Host-only check of the execution plan (no device work, usable without a
  * GPU): builds, for a mesh and parameters, the cluster tree, the block
  * partition (Section "H2-Matrix Compression"), the passes of the product and
- * the dataflow ticket order (with and without the near field) exactly as
- * h2_assemble does, with the ticket order simulated for `workers` concurrent
+ * the dataflow ticket order (with and without the near field, and merged
+ * with a second copy of itself as a batched launch merges operators) exactly
+ * as h2_assemble and h2_matvec_batched do, with the ticket order simulated for `workers` concurrent
  * CTAs, and checks the invariants the product kernels rely on, independently
  * of the code that built them: every chunk a legal bulk copy (16-byte aligned
  * source and size, within one stage, input rows on 4-row boundaries, one

@@ -6,8 +6,9 @@
 // admissible blocks and exact near blocks), the passes of the product (upward
 // leaf projection and transfers, coupling, downward transfers, near field,
 // leaf expansion) and the dataflow ticket order (with and without the near
-// field, as the split form uses it) come from the same host code as in
-// h2_assemble.  The checks:
+// field, as the split form uses it, and the merged order of a batched launch)
+// come from the same host code as in h2_assemble and h2_matvec_batched.  The
+// checks:
 //   * every chunk is a legal bulk copy (16-byte aligned source and size, at
 //     most one stage, its pieces inside it, input rows on 4-row boundaries,
 //     one piece type per chunk, one accumulator kind per segment);
@@ -141,6 +142,14 @@ int h2_plan_check(const double* xyz, int64_t n_vertices, const int32_t* tri, int
         if (out->makespan_us < 0.0) ++bad;
         else bad += check_flow(*op, full);
         if (ms_split >= 0.0) bad += check_flow(*op, split);
+        // the merged order of a batched launch (here the operator twice: the
+        // second copy's regions follow the first's)
+        h2::FlowOut twice;
+        if (h2::build_flow_multi({op, op}, fm, twice, false) < 0.0) ++bad;
+        else {
+            bad += check_flow(*op, twice);
+            if (twice.nreg != 2 * full.nreg || twice.seg.size() != 2 * full.seg.size()) ++bad;
+        }
         out->n_clusters = op->nc;
         out->n_levels = op->nlevels;
         out->n_far_blocks = (int64_t)op->far_t.size();
