@@ -37,7 +37,7 @@ int check_chunks(const h2_handle& op, const std::vector<h2::Chunk>& chunks, cons
             int cols = 0;
             for (int q = 0; q < c.npieces && ok; ++q) {
                 const h2::Piece& p = pieces[(size_t)c.piece0 + q];
-                ok = p.in_row >= 0 && p.in_row % 4 == 0 && p.smem_off % 16 == 0 && p.smem_off >= 0 &&
+                ok = p.ncols >= 1 && p.in_row >= 0 && p.in_row % 4 == 0 && p.smem_off % 16 == 0 && p.smem_off >= 0 &&
                      p.smem_off < c.bytes && (int64_t)p.in_row + p.ncols <= op.ws_rows - 4 && p.type == c.type0;
                 cols += p.ncols;
             }
@@ -106,7 +106,9 @@ int h2_plan_check(const double* xyz, int64_t n_vertices, const int32_t* tri, int
         !(p.box_inflation > 0.0) || p.box_inflation > 1.0 || p.max_rhs < 1 || p.max_rhs > H2_MAX_RHS ||
         p.precision < H2_FP64 || p.precision > H2_BF16X3 ||
         (p.coupling != H2_COUPLING_STORED && p.coupling != H2_COUPLING_ON_THE_FLY) ||
-        (p.coupling == H2_COUPLING_ON_THE_FLY && p.precision != H2_FP32))
+        (p.coupling == H2_COUPLING_ON_THE_FLY && p.precision != H2_FP32) ||
+        (p.schedule != H2_SCHEDULE_FLOW && p.schedule != H2_SCHEDULE_LEVELS) || (p.autotune != 0 && p.autotune != 1) ||
+        (p.near_field != H2_NEAR_FP64 && p.near_field != H2_NEAR_F32PAIR))
         return H2_ERR_INVALID_ARG;
     h2_handle* geom = new (std::nothrow) h2_handle();
     h2_handle* op = new (std::nothrow) h2_handle();

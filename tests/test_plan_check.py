@@ -92,3 +92,5 @@ def test_invalid_meshes_and_parameters_are_refused(L):
         pkg.h2_plan_check(mesh.xyz, mesh.tri, m=9)
     with pytest.raises(pkg.H2Error):
         pkg.h2_plan_check(mesh.xyz, mesh.tri, 0)
+    with pytest.raises(pkg.H2Error):
+        pkg.h2_plan_check(mesh.xyz, mesh.tri, schedule=7)
