@@ -170,6 +170,25 @@ def test_sphere_dipole_eigenvalue_converges():
     assert errs[2] < 3e-3
 
 
+@pytest.mark.parametrize("key,harmonic", [
+    ("sphere_l2_eigenvalue", lambda p: 3.0 * p[:, 2] ** 2 - 1.0),
+    ("sphere_l2_eigenvalue", lambda p: p[:, 0] * p[:, 1]),
+    ("sphere_l3_eigenvalue", lambda p: 5.0 * p[:, 2] ** 3 - 3.0 * p[:, 2]),
+])
+def test_sphere_higher_harmonics_are_eigenvectors(key, harmonic):
+    """Degree-2 and degree-3 spherical harmonics at the nodes are mapped to
+    -(l+1)/(2l+1) times themselves, up to the O(h^2) error of the flat mesh."""
+    lam = GOLDEN[key]["value"]
+    errs = []
+    for lvl in (2, 3, 4):
+        m = synth.icosphere(lvl)
+        p = m.xyz / np.linalg.norm(m.xyz, axis=1)[:, None]
+        y0 = harmonic(p)
+        y = oracle.dense_matvec(m.xyz, m.tri, y0[None, :])[0]
+        errs.append(np.linalg.norm(y - lam * y0) / np.linalg.norm(lam * y0))
+    assert errs[1] < errs[0] / 3.5 and errs[2] < errs[1] / 3.5 and errs[2] < 3e-3, errs
+
+
 def test_sphere_demag_factor_converges_to_one_third():
     target = GOLDEN["sphere_demag_factor"]["value"]
     errs = []
