@@ -573,3 +573,131 @@ def test_h2_far_block_equals_explicit_product():
         Mblk = Mfull[np.ix_(ti, si)]
         errs.append(np.linalg.norm(V @ S @ W.T - Mblk) / np.linalg.norm(Mblk))
     assert errs[0] < 2e-2 and errs[1] < errs[0] / 5.0, errs
+
+
+# ------------------------------------------------------- boxes and admissibility
+# Section "H2-Matrix Compression" asks only for "well-separated" clusters; the
+# reading taken is: (t, s) admissible iff max(diam B_t, diam B_s) <= eta *
+# dist(B_t, B_s), diam the box diagonal, dist the Euclidean distance between
+# the two closed boxes.  The cases below are computed by hand, chosen so that
+# the plausible slips (centre-to-centre distance, the largest or the sum of the
+# per-axis gaps, the smaller or only one box's diameter) each flip one answer.
+def _box(lo, hi):
+    return np.array(list(lo) + list(hi), dtype=np.float64)
+
+
+UNIT = _box((0, 0, 0), (1, 1, 1))
+ADMISSIBILITY_CASES = [
+    # (box t, box s, eta, expected, why)
+    # gap 2 along x: diam sqrt(3) = 1.732, dist 2 (centre distance 3)
+    (UNIT, _box((3, 0, 0), (4, 1, 1)), 1.0, True, "1.732 <= 1 * 2"),
+    (UNIT, _box((3, 0, 0), (4, 1, 1)), 0.8, False, "1.732 > 0.8 * 2 (centre distance would give 2.4)"),
+    (UNIT, _box((3, 0, 0), (4, 1, 1)), 0.87, True, "1.732 <= 0.87 * 2 = 1.74"),
+    (UNIT, _box((3, 0, 0), (4, 1, 1)), 0.86, False, "1.732 > 0.86 * 2 = 1.72"),
+    # overlapping and touching boxes: dist 0, never admissible
+    (UNIT, _box((0.5, 0.5, 0.5), (1.5, 1.5, 1.5)), 1e6, False, "overlap: dist 0"),
+    (UNIT, _box((1, 0, 0), (2, 1, 1)), 1e6, False, "shared face: dist 0"),
+    (UNIT, _box((1, 1, 1), (2, 2, 2)), 1e6, False, "shared corner: dist 0"),
+    (UNIT, UNIT, 1e6, False, "the same box"),
+    # gaps on two axes (x 1, y 2, z overlapping): dist sqrt(5) = 2.2361;
+    # sqrt(3) <= eta sqrt(5) iff eta >= 0.77460 (largest gap alone: 0.866;
+    # sum of the gaps: 0.577; centre distance sqrt(4 + 9 + 0.25): 0.476)
+    (UNIT, _box((2, 3, 0.5), (3, 4, 1.5)), 0.78, True, "1.732 <= 0.78 * 2.236 = 1.744"),
+    (UNIT, _box((2, 3, 0.5), (3, 4, 1.5)), 0.77, False, "1.732 > 0.77 * 2.236 = 1.722"),
+    # gaps on all three axes (1, 1, 1): dist sqrt(3), so admissible iff eta >= 1
+    (UNIT, _box((2, 2, 2), (3, 3, 3)), 1.0, True, "sqrt(3) <= 1 * sqrt(3)"),
+    (UNIT, _box((-2, -2, -2), (-1, -1, -1)), 0.999, False, "sqrt(3) > 0.999 sqrt(3)"),
+    # unequal boxes: the larger diameter decides (sqrt(18) = 4.2426 vs sqrt(3)), dist 2:
+    # admissible iff eta >= 2.1213, in either order
+    (_box((0, 0, 0), (4, 1, 1)), _box((6, 0, 0), (7, 1, 1)), 2.13, True, "4.243 <= 2.13 * 2"),
+    (_box((0, 0, 0), (4, 1, 1)), _box((6, 0, 0), (7, 1, 1)), 2.11, False, "4.243 > 2.11 * 2"),
+    (_box((6, 0, 0), (7, 1, 1)), _box((0, 0, 0), (4, 1, 1)), 2.11, False, "same pair, swapped"),
+    (_box((6, 0, 0), (7, 1, 1)), _box((0, 0, 0), (4, 1, 1)), 2.13, True, "same pair, swapped"),
+    # a flat face cluster's box after inflation: [0,1]^2 x [-0.125, 0.125] (each
+    # side at least 0.25 x the longest), diam sqrt(2.0625) = 1.43614 (uninflated:
+    # sqrt(2) = 1.41421); twin box at gap 1.5 along x
+    (_box((0, 0, -0.125), (1, 1, 0.125)), _box((2.5, 0, -0.125), (3.5, 1, 0.125)), 0.96, True,
+     "1.4361 <= 0.96 * 1.5 = 1.44"),
+    (_box((0, 0, -0.125), (1, 1, 0.125)), _box((2.5, 0, -0.125), (3.5, 1, 0.125)), 0.95, False,
+     "1.4361 > 0.95 * 1.5 = 1.425 (the uninflated 1.4142 would pass)"),
+]
+
+
+@pytest.mark.parametrize("bt,bs,eta,want,why", ADMISSIBILITY_CASES,
+                         ids=[f"{i}" for i in range(len(ADMISSIBILITY_CASES))])
+def test_admissibility_hand_computed_boxes(bt, bs, eta, want, why):
+    assert oracle.admissible(bt, bs, eta) is want, why
+
+
+def _inflated_support_box(xyz, tri, nodes, rho=0.25):
+    """Bounding box of every triangle touching `nodes` (the support of their
+    hat functions), each side widened about its centre to rho x the longest."""
+    tris = np.where(np.isin(tri, nodes).any(axis=1))[0]
+    pts = xyz[tri[tris]].reshape(-1, 3)
+    lo, hi = pts.min(axis=0), pts.max(axis=0)
+    w = hi - lo
+    need = rho * w.max()
+    c = 0.5 * (lo + hi)
+    lo = np.where(w < need, c - 0.5 * need, lo)
+    hi = np.where(w < need, c + 0.5 * need, hi)
+    return np.concatenate([lo, hi])
+
+
+@pytest.mark.parametrize("mk,leaf,has_flat", [(lambda: synth.cube_surface(8), 16, True),
+                                              (lambda: synth.film_box(12, 2), 24, True),
+                                              (lambda: synth.box_surface(10, 20, 1, 10.0, 20.0, 1.0), 32, True),
+                                              (lambda: synth.icosphere(2), 8, False)])
+def test_cluster_boxes_are_the_inflated_supports(mk, leaf, has_flat):
+    """Every cluster's interpolation box is the support box of its nodes, with
+    sides below rho = 0.25 x the longest widened about their centre (flat face
+    clusters of the cube, the film and the prism get thickness 0.25 x their
+    extent, not 0), restated here from that rule alone."""
+    m = mk()
+    h = oracle.H2Oracle(m.xyz, m.tri, 2, leaf, 2.0, store=False)
+    t = h.tree()
+    flat = 0
+    for c in range(h.n_clusters):
+        nodes = t["perm"][t["start"][c]:t["start"][c] + t["size"][c]]
+        want = _inflated_support_box(m.xyz, m.tri, nodes)
+        scale = np.max(np.abs(want)) + 1.0
+        assert np.max(np.abs(t["box"][c] - want)) <= 1e-14 * scale, (c, t["box"][c], want)
+        w = want[3:] - want[:3]
+        flat += int(np.isclose(w.min(), 0.25 * w.max()))
+    assert (flat > 0) == has_flat   # flat face clusters were widened
+
+
+def test_block_partition_follows_the_hand_checked_predicate():
+    """The block recursion's far / near decisions on a flat-faced mesh, with the
+    predicate evaluated here from per-axis gaps and diagonals (independent of
+    the oracle's admissibility routine): every far block is admissible, every
+    near block inadmissible, and the pair each block was split from (its
+    parents, a leaf standing for itself) was inadmissible."""
+    m = synth.cube_surface(6)
+    eta = 2.0
+    h = oracle.H2Oracle(m.xyz, m.tri, 2, 8, eta, store=False)
+    t = h.tree()
+    b = h.blocks()
+    box = t["box"]
+
+    def adm(p, q):
+        a, c = box[p], box[q]
+        gap = np.maximum(0.0, np.maximum(c[:3] - a[3:], a[:3] - c[3:]))
+        diam = max(np.linalg.norm(a[3:] - a[:3]), np.linalg.norm(c[3:] - c[:3]))
+        return diam <= eta * np.linalg.norm(gap)
+
+    for kind in ("far", "near"):
+        for tt, ss in zip(b[kind + "_t"], b[kind + "_s"]):
+            assert adm(tt, ss) == (kind == "far"), (kind, tt, ss)
+            if tt == 0 and ss == 0:
+                continue
+            # candidate parents: (parent t, parent s), or one side kept when it was a leaf
+            cands = []
+            pt, ps = t["parent"][tt], t["parent"][ss]
+            if pt >= 0 and ps >= 0:
+                cands.append((pt, ps))
+            if pt >= 0 and t["child0"][ss] < 0:
+                cands.append((pt, ss))
+            if ps >= 0 and t["child0"][tt] < 0:
+                cands.append((tt, ps))
+            assert any(not adm(p, q) for p, q in cands), (kind, tt, ss, cands)
+    assert h.n_far > 0 and h.n_near > 0
