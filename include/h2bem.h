@@ -48,7 +48,7 @@ typedef enum {
     H2_ERR_OOM = -5,                  /* device or host allocation failed */
     H2_ERR_CUDA = -6,                 /* a CUDA runtime call failed */
     H2_ERR_TIMEOUT = -7,              /* a bounded device-side wait gave up */
-    H2_ERR_RHS_EXCEEDS_MAX = -8,      /* r > h2_params.max_rhs */
+    H2_ERR_RHS_EXCEEDS_MAX = -8,      /* r > h2_params.max_rhs (h2_matvec_noalloc: its own limit) */
     H2_ERR_WRONG_HANDLE = -9,         /* geometry given where an operator is needed, or vice versa */
     H2_ERR_SCRATCH_LIMIT = -10        /* h2_matvec_noalloc: problem larger than its fixed scratch */
 } h2_status;
@@ -64,16 +64,20 @@ typedef enum {
  *             tensor cores (tcgen05) as three TF32 products per term
  *             (hi*hi + hi*lo + lo*hi, hi = the nearest TF32 value, lo = the
  *             nearest TF32 value of the remainder), FP32 accumulation.
- *  H2_BF16X3: coupling and transfer matrices stored as BF16 pairs hi + lo
- *             (hi = bf16(a), lo = bf16(a - hi), 4 bytes per entry) and
- *             multiplied on the tensor cores as hi*hi + hi*lo + lo*hi with the
- *             vectors split the same way, FP32 accumulation.  Leaf bases FP32.
+ *  H2_BF16X3: coupling matrices stored as BF16 pairs hi + lo (hi = bf16(a),
+ *             lo = bf16(a - hi), 4 bytes per entry, |a - hi - lo| <= 2^-18 |a|)
+ *             and multiplied on the tensor cores with the FP32 vectors split
+ *             into three BF16 words x = xh + xm + xl (exact), as
+ *             hi*(xh + xm + xl) + lo*(xh + xm), FP32 accumulation; transfer
+ *             matrices and leaf bases FP32 on the CUDA cores (the same 4 bytes
+ *             per entry).
  * For products of at most 4 right-hand sides the H2_TF32X3 and H2_BF16X3 tiles
  * are multiplied on the CUDA cores (the same stored values, FP32 products and
  * accumulation), where one tensor-core instruction of so few columns costs as
  * much as one of 128; h2_autotune may choose the tensor cores instead.
- * The reduced forms target a relative error <= 1e-5 against the FP64 form
- * (BF16 hi + lo keeps about 17 significant bits of each entry). */
+ * The reduced forms target a relative error <= 1e-5 against the FP64 form;
+ * BF16 hi + lo keeps about 17 significant bits of each coupling entry, which
+ * the far-field sums amplify to 5e-6 .. 1.3e-5 on the benchmark meshes. */
 typedef enum { H2_FP64 = 0, H2_FP32 = 1, H2_TF32X3 = 2, H2_BF16X3 = 3 } h2_precision;
 
 typedef struct {
@@ -186,8 +190,12 @@ int h2_matvec_batched(h2_handle* const* ops, int32_t n_ops, const double* const*
  * reserved all device memory in advance, or an application whose device
  * memory belongs to its own pool allocator).  The paper has no counterpart:
  * this is a property of the library, not of the method.
- *   u1, u2: DEVICE pointers only, r x N doubles as in h2_matvec; 1 <= r <= 32
- *           (independent of max_rhs).  Asynchronous on `cuda_stream`.
+ *   u1, u2: DEVICE pointers only, r x N doubles as in h2_matvec.
+ *   r:      1 <= r <= 8 for an operator assembled with max_rhs <= 8, else
+ *           1 <= r <= 32 (either may exceed max_rhs); a larger r returns
+ *           H2_ERR_RHS_EXCEEDS_MAX without launching anything.
+ * The calling thread's current device must be the operator's device
+ * (H2_ERR_INVALID_ARG otherwise).  Asynchronous on `cuda_stream`.
  * The workspace is a fixed array of 4,194,304 doubles (32 MiB) inside the
  * library, present on every GPU that loads it until the process exits.
  * It must hold W = rows x r doubles, rows = (the mesh nodes, each leaf
@@ -290,16 +298,20 @@ int h2_fault_inject_stall(h2_handle* op, int32_t enable);
  * recorded so far. */
 int h2_profile_enable(h2_handle* op, int32_t enable);
 
-/* Synchronises on the recorded events and returns, per launch of one
- * h2_matvec in launch order (entry 0 = the input gather, then one entry per
- * pass, or one entry for the single flow kernel), the pass kind (0 gather,
- * 1 upward leaf projection, 2 upward transfer, 3 coupling, 4 downward
- * transfer, 5 near field, 6 leaf expansion, 7 the whole flow kernel),
- * the total milliseconds over all recorded calls, the matrix bytes and the
- * multiply-adds (per right-hand side) of one launch, and its grid size.
- * Arrays hold `capacity` entries (any may be NULL); *n_entries is the number
- * of launches per call and *n_calls the number of recorded calls.  Clears the
- * recorded events. */
+/* Synchronises on the recorded events and returns, per kernel launch of one
+ * h2_matvec in launch order (the input gather, then one entry per pass, or
+ * one entry for the single flow kernel; the split form: gather, near field,
+ * far-field flow kernel, joining addition, per product of at most 16
+ * right-hand sides), the kind (0 gather, 1 upward leaf projection, 2 upward
+ * transfer, 3 coupling, 4 downward transfer, 5 near field, 6 leaf expansion,
+ * 7 the whole flow kernel, 8 the split form's near field, 9 its far-field
+ * flow kernel, 10 its addition), the total milliseconds over all recorded
+ * calls (each launch timed by events recorded before and after it on the
+ * stream it runs on), the matrix bytes and the multiply-adds (per
+ * right-hand side) of one launch, and its grid size.  Arrays hold
+ * `capacity` entries (any may be NULL); *n_entries is the number of launches
+ * per call and *n_calls the number of recorded calls.  Clears the recorded
+ * events. */
 int h2_profile_read(h2_handle* op, int32_t capacity, int32_t* kind, double* ms_total,
                     int64_t* bytes, int64_t* macs, int32_t* grid, int32_t* n_calls,
                     int32_t* n_entries);

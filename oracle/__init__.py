@@ -8,7 +8,8 @@ The arithmetic lives in ``h2_oracle.c`` (plain C, FP64, OpenMP over rows),
 compiled with gcc into ``oracle/_build``; this module marshals numpy arrays.
 Equation names refer to arXiv:1811.05731.
 
-* ``psi``: interior solid angle Psi at each node (Eq. mainInt).
+* ``psi``: interior solid angle Psi at each node (Eq. mainInt); ``psi_at``
+  at selected nodes only.
 * ``lindholm``: corner weights of one triangle seen from one point (K entries,
   Eq. matrix_definition, Lindholm's closed form).
 * ``dense_matrix`` / ``dense_matvec`` / ``dense_rows``: M = K + D (Eq. denseMat).
@@ -70,6 +71,7 @@ def _lib():
             L.o_solid_angle.argtypes = [_d, _d, _d, _d]
             L.o_lindholm.argtypes = [_d, _d, _d, _d, _d]
             L.o_psi.argtypes = [ctypes.c_int64, _d, ctypes.c_int64, _i32, _d]
+            L.o_psi_nodes.argtypes = [_d, ctypes.c_int64, _i32, ctypes.c_int64, _i64, _d]
             L.o_dense_matrix.argtypes = [ctypes.c_int64, _d, ctypes.c_int64, _i32, _d, _d]
             L.o_dense_rows.argtypes = [ctypes.c_int64, _d, ctypes.c_int64, _i32, _d,
                                        ctypes.c_int64, _i64, _d]
@@ -140,6 +142,16 @@ def psi(xyz, tri) -> np.ndarray:
     return out
 
 
+def psi_at(xyz, tri, nodes) -> np.ndarray:
+    """Psi at the given nodes only (NaN elsewhere): O(T) per node, for sampled rows of large meshes."""
+    xyz = _f64(xyz)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+    out = np.full(xyz.shape[0], np.nan)
+    _lib().o_psi_nodes(_pd(xyz), tri.shape[0], _pi32(tri), nodes.size, _pi64(nodes), _pd(out))
+    return out
+
+
 def dense_matrix(xyz, tri, psi_v=None) -> np.ndarray:
     xyz = _f64(xyz)
     tri = np.ascontiguousarray(tri, dtype=np.int32)
@@ -151,9 +163,10 @@ def dense_matrix(xyz, tri, psi_v=None) -> np.ndarray:
 
 
 def dense_rows(xyz, tri, rows, psi_v=None) -> np.ndarray:
+    """Rows of M at the given nodes (Psi is needed at those nodes only)."""
     xyz = _f64(xyz)
     tri = np.ascontiguousarray(tri, dtype=np.int32)
-    ps = psi(xyz, tri) if psi_v is None else _f64(psi_v)
+    ps = psi_at(xyz, tri, rows) if psi_v is None else _f64(psi_v)
     rows = np.ascontiguousarray(rows, dtype=np.int64)
     out = np.zeros((rows.size, xyz.shape[0]))
     _lib().o_dense_rows(xyz.shape[0], _pd(xyz), tri.shape[0], _pi32(tri), _pd(ps),

@@ -152,6 +152,12 @@ void o_psi(int64_t N, const double* xyz, int64_t T, const int32_t* tri, double* 
     for (int64_t i = 0; i < N; ++i) psi[i] = psi_one(i, xyz, T, tri);
 }
 
+/* Psi at the listed nodes only: psi[nodes[q]] for q < n (other entries untouched). */
+void o_psi_nodes(const double* xyz, int64_t T, const int32_t* tri, int64_t n, const int64_t* nodes, double* psi) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < n; ++q) psi[nodes[q]] = psi_one(nodes[q], xyz, T, tri);
+}
+
 /* One full row of M: row[j] = M_ij for all j (row has N entries, zeroed here). */
 static void dense_row(int64_t i, int64_t N, const double* xyz, int64_t T, const int32_t* tri,
                       const double* psi, double* row) {

@@ -269,9 +269,10 @@ int h2_device_status(h2_handle* op) {
 int h2_profile_enable(h2_handle* op, int32_t enable) {
     if (!op) return H2_ERR_INVALID_ARG;
     if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
+    std::vector<h2::ProfLaunch> launches;
     std::vector<double> ms;
     int n = 0;
-    int rc = h2::read_profile(op, ms, n);   // drops what was recorded so far
+    int rc = h2::read_profile(op, launches, ms, n);   // drops what was recorded so far
     if (rc != H2_OK) return rc;
     op->prof_enabled = enable ? 1 : 0;
     return H2_OK;
@@ -281,32 +282,20 @@ int h2_profile_read(h2_handle* op, int32_t capacity, int32_t* kind, double* ms_t
                     int64_t* macs, int32_t* grid, int32_t* n_calls, int32_t* n_entries) {
     if (!op || !n_calls || !n_entries) return H2_ERR_INVALID_ARG;
     if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
+    std::vector<h2::ProfLaunch> launches;
     std::vector<double> ms;
     int n = 0;
-    int rc = h2::read_profile(op, ms, n);
+    int rc = h2::read_profile(op, launches, ms, n);
     if (rc != H2_OK) return rc;
     *n_calls = n;
     *n_entries = (int32_t)ms.size();
     for (int32_t i = 0; i < (int32_t)ms.size() && i < capacity; ++i) {
-        int32_t kd = h2::PASS_PROLOGUE, gr = 0;
-        int64_t by = 0, mc = 0;
-        if (i > 0 && op->use_flow) {
-            kd = h2::PASS_FLOW;
-            by = op->bytes_streamed;
-            mc = op->macs;
-            gr = op->flow_grid;
-        } else if (i > 0) {
-            const h2::Pass& p = op->passes[(size_t)i - 1];
-            kd = p.kind;
-            by = p.bytes;
-            mc = p.macs;
-            gr = p.grid;
-        }
-        if (kind) kind[i] = kd;
+        const h2::ProfLaunch& L = launches[(size_t)i];
+        if (kind) kind[i] = L.kind;
         if (ms_total) ms_total[i] = ms[(size_t)i];
-        if (bytes) bytes[i] = by;
-        if (macs) macs[i] = mc;
-        if (grid) grid[i] = gr;
+        if (bytes) bytes[i] = L.bytes;
+        if (macs) macs[i] = L.macs;
+        if (grid) grid[i] = L.grid;
     }
     return H2_OK;
 }

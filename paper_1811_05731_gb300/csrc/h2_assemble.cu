@@ -510,7 +510,8 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
     // the operator's far-field format
     const int prec = op->params.precision;
     const int f32 = prec == H2_FP64 ? 0 : 1;
-    const int tt = prec == H2_FP64 ? PIECE_F64 : prec == H2_FP32 ? PIECE_F32 : prec == H2_TF32X3 ? PIECE_TF32 : PIECE_BF16X3;
+    const int tt = coupling_piece_type(prec);    // coupling blocks
+    const int te = transfer_piece_type(prec);    // transfers
     int rc;
 
     H2_CUDA_TRY(cudaMalloc((void**)&op->d_arena, (size_t)std::max<int64_t>(op->arena_bytes, 16)));
@@ -616,7 +617,7 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
     TransferItem* d_ti = nullptr;
     if ((rc = upload(ti, &d_ti, s))) { cleanup(); return rc; }
     tmp.push_back(d_ti);
-    if (!ti.empty()) k_transfer<<<(unsigned)ti.size(), kb, 0, s>>>(d_ti, m, op->d_arena, tt);
+    if (!ti.empty()) k_transfer<<<(unsigned)ti.size(), kb, 0, s>>>(d_ti, m, op->d_arena, te);
 
     // coupling
     std::vector<CouplingItem> ci(op->far_t.size());

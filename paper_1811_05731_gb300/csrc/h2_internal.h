@@ -54,6 +54,16 @@ enum PieceType : int32_t { PIECE_F64 = 0, PIECE_F32 = 1, PIECE_TF32 = 2, PIECE_B
 // operator's per-cluster node table.
 
 inline __host__ __device__ bool piece_tc(int type) { return type == PIECE_TF32 || type == PIECE_BF16X3; }
+// Stored format of the coupling blocks S_ts of an operator of precision `prec`.
+inline int coupling_piece_type(int prec) {
+    return prec == H2_FP64 ? PIECE_F64 : prec == H2_FP32 ? PIECE_F32 : prec == H2_TF32X3 ? PIECE_TF32 : PIECE_BF16X3;
+}
+// Stored format of the transfer matrices E_c.  BF16 hi + lo operators keep
+// them in FP32 (the same 4 bytes per entry) on the CUDA cores: a transfer's
+// rounding reaches every level above and below it, and 17-bit transfers
+// compounded over the tree's 12-16 levels would exceed the 1e-5 budget by
+// themselves; they are about a tenth of the far field's entries.
+inline int transfer_piece_type(int prec) { return prec == H2_BF16X3 ? PIECE_F32 : coupling_piece_type(prec); }
 // Rows of a tensor-core tile (the MMA's M) for a block of `nrows` rows.
 inline __host__ __device__ int tc_rows(int nrows) { return nrows <= 64 ? 64 : 128; }
 // Columns (the MMA's K) multiplied by one tcgen05.mma.
@@ -117,6 +127,17 @@ struct Segment {
 enum PassKind : int32_t {
     PASS_PROLOGUE = 0, PASS_UP_LEAF = 1, PASS_UP_TRANSFER = 2, PASS_COUPLING = 3,
     PASS_DOWN_TRANSFER = 4, PASS_LEAF_NEAR = 5, PASS_LEAF_EXPAND = 6, PASS_FLOW = 7,
+    // launches of the split form: the near field on the operator's second
+    // stream, the dataflow launch of everything else, the joining addition
+    PASS_SPLIT_NEAR = 8, PASS_SPLIT_FAR = 9, PASS_SPLIT_ADD = 10,
+};
+
+// One profiled kernel launch: events recorded before and after it on the
+// stream it was launched on, with what it computes.
+struct ProfLaunch {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int32_t kind = 0, grid = 0, r = 0;
+    int64_t bytes = 0, macs = 0;   // matrix bytes read, multiply-adds per right-hand side
 };
 
 struct FlowSeg;
@@ -292,7 +313,7 @@ struct h2_handle {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // per-pass timing with CUDA events (profiling aid, off by default)
     int prof_enabled = 0;
-    std::vector<std::vector<cudaEvent_t>> prof_calls;   // events of each profiled call
+    std::vector<std::vector<h2::ProfLaunch>> prof_calls;   // launches of each profiled call
     std::vector<cudaEvent_t> prof_pool;
 };
 
@@ -329,7 +350,7 @@ int upload_plan(h2_handle* op);
 int matvec_device(h2_handle* op, const double* u1, double* u2, int r, cudaStream_t s);
 void release_graph(h2_handle* op);
 void release_profile(h2_handle* op);
-int read_profile(h2_handle* op, std::vector<double>& ms, int& ncalls);
+int read_profile(h2_handle* op, std::vector<ProfLaunch>& launches, std::vector<double>& ms, int& ncalls);
 size_t pass_smem_bytes(const h2_handle* op, int rt);
 int flow_model(h2_handle* op, FlowModel& fm);   // CTAs and rates of the device
 // One persistent launch over several operators (h2_matvec_batched).

@@ -146,12 +146,13 @@ struct KArgs {
     int stage_bytes;
     int tc;                    // the operator has tensor-core segments
     int tc_alo_bytes;          // shared memory for the TF32 lo parts of a chunk
-    int tc_b_bytes;            // shared memory for each of the B hi / lo operands
+    int tc_b_bytes;            // shared memory for the B operand (all its parts) of a chunk
+    int tc_parts;              // most vector parts of a launch's tiles (3: BF16 hi, mid, lo; 2: TF32 hi, lo)
     int tc_sets;               // operand sets (2: the next chunk is prepared while the tensor core works)
     int tc_cols;               // TMEM columns per CTA (power of 2, at most 512 / resident CTAs per SM)
-    int tc_nacc;               // accumulators of the hi*hi products (K steps round-robin)
-    int tc_ncorr;              // accumulators of the correction products (round-robin)
-    int tc_np;                 // accumulator width: right-hand sides rounded up to 16
+    int tc_nacc;               // accumulators of the A_hi products (K steps round-robin)
+    int tc_ncorr;              // accumulators of the A_lo correction products (round-robin)
+    int tc_np;                 // columns of one vector part: right-hand sides rounded up to 16
     int tc_cuda;               // 1: tensor-core tiles multiplied on the CUDA cores (small r)
     int nops;                  // operators of the launch (several: a batched product)
     OpCtx ctx[H2_MAX_BATCH];
@@ -595,8 +596,8 @@ __host__ __device__ constexpr int red_rhs(int rt) { return rt <= 8 ? rt : 4; }
 //   stages x stage_bytes             matrix chunks (bulk copies)
 //   stages x xin_bytes(RT)           the chunks' input values
 //   2 x kConsumers*red_rhs(RT)*8     partial sums of the row groups (two buffers)
-//   tc_sets x (tc_alo_bytes + 2 x tc_b_bytes)   tensor-core operands (TF32 lo parts of A,
-//                                    B with its hi rows and its lo rows)
+//   tc_sets x (tc_alo_bytes + tc_b_bytes)   tensor-core operands (TF32 lo parts of A,
+//                                    B with the rows of its vector parts)
 //   stages x 2 + 5 mbarriers         full[], empty[], segment, operands-ready[2], products-done[2]
 //
 // Warp specialisation.  The producer warp (the last warp) walks this CTA's
@@ -624,7 +625,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
     // tensor-core operands after the partial sums;
     // operand set q: [lo parts of A][B: hi rows, lo rows] at tc_base + q * tc_set_bytes
     unsigned char* tc_base = reinterpret_cast<unsigned char*>(red + kRedBuffers * kConsumers * RR);
-    const size_t tc_set_bytes = (size_t)a.tc_alo_bytes + 2 * (size_t)a.tc_b_bytes;
+    const size_t tc_set_bytes = (size_t)a.tc_alo_bytes + (size_t)a.tc_b_bytes;
     const size_t red_span = (size_t)kRedBuffers * kConsumers * RR * sizeof(double);
     const size_t tc_span = (size_t)a.tc_sets * tc_set_bytes;
     uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(red) + red_span + tc_span);
@@ -826,6 +827,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                 const int Np = Mp == 64 ? (r + 7) / 8 * 8 : (r + 15) / 16 * 16;
                 const int ks = tc_kstep(type);
                 const int bes = type == PIECE_TF32 ? 4 : 2;
+                // vector parts: TF32 hi, lo; BF16 hi, mid, lo (exact for the FP32 vector)
+                const int ph = type == PIECE_TF32 ? 2 : 3;
                 // one operand set: wait until the previous chunk's products are done
                 if (a.tc_sets == 1 && !release_pending()) {
                     atomicExch(a.err, 1);
@@ -834,8 +837,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                 }
                 unsigned char* set = tc_base + (size_t)(tcn % a.tc_sets) * tc_set_bytes;
                 unsigned char* t_alo = set;
-                unsigned char* t_b = set + a.tc_alo_bytes;   // B: 2 Np rows, hi parts then lo parts
-                const int N2 = 2 * Np;
+                unsigned char* t_b = set + a.tc_alo_bytes;   // B: ph x Np rows, part by part
+                const int Nt = ph * Np;
                 // operands: written by consumer warps 1..7 while warp 0 issues the
                 // previous chunk's products
                 const int wt = tid - 32, nwt = kConsumers - 32;
@@ -850,12 +853,16 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                                             tf32_rn(v.w - h.w));
                     }
                 }
-                // B operand: rows n < r (right-hand sides, hi parts) and Np + n (lo
-                // parts), K = the pieces' input rows (each piece padded to whole K steps
-                // with zeros).  Rows r..Np-1 and Np+r..2Np-1 are not written: they only
-                // reach accumulator columns that are never read.  A work unit is one
-                // 16-byte core row: right-hand side n, `per` consecutive K rows (8 BF16
-                // or 4 TF32 values), written with one vector store per part.
+                // B operand: part p of right-hand side n is row p * Np + n, K = the
+                // pieces' input rows (each piece padded to whole K steps with zeros).
+                // Rows r..Np-1 of each part are not written: they only reach
+                // accumulator columns that are never read.  A work unit is one 16-byte
+                // core row: right-hand side n, `per` consecutive K rows (8 BF16 or 4
+                // TF32 values), written with one vector store per part.  TF32: hi =
+                // RN_tf32(x), lo = RN_tf32(x - hi).  BF16: hi = bf16(x), mid =
+                // bf16(x - hi), lo = bf16(x - hi - mid); both differences are exact in
+                // FP32 and the last one has at most 8 significant bits, so hi + mid +
+                // lo = x exactly.
                 if (wt >= 0) {
                     const int per = 16 / bes;
                     const int nb = r;
@@ -868,8 +875,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                         for (int u = wt; u < units; u += nwt) {
                             const int kg = u / nb, n = u - kg * nb;   // K group, right-hand side
                             const int j0 = kg * per;
-                            const int off = b_offset(n, kb + j0, N2, bes);
-                            const int offl = b_offset(Np + n, kb + j0, N2, bes);
+                            const int off0 = b_offset(n, kb + j0, Nt, bes);
+                            const int off1 = b_offset(Np + n, kb + j0, Nt, bes);
                             if (type == PIECE_TF32) {
                                 float h[4], l[4];
 #pragma unroll
@@ -878,18 +885,22 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                                     h[e] = tf32_rn(x);
                                     l[e] = tf32_rn(x - h[e]);
                                 }
-                                *reinterpret_cast<float4*>(t_b + off) = make_float4(h[0], h[1], h[2], h[3]);
-                                *reinterpret_cast<float4*>(t_b + offl) = make_float4(l[0], l[1], l[2], l[3]);
+                                *reinterpret_cast<float4*>(t_b + off0) = make_float4(h[0], h[1], h[2], h[3]);
+                                *reinterpret_cast<float4*>(t_b + off1) = make_float4(l[0], l[1], l[2], l[3]);
                             } else {
-                                __align__(16) __nv_bfloat16 h[8], l[8];
+                                const int off2 = b_offset(2 * Np + n, kb + j0, Nt, bes);
+                                __align__(16) __nv_bfloat16 h[8], mi[8], l[8];
 #pragma unroll
                                 for (int e = 0; e < 8; ++e) {
                                     const float x = (j0 + e < P.ncols && n < r) ? xp[(j0 + e) * r + n] : 0.0f;
                                     h[e] = __float2bfloat16_rn(x);
-                                    l[e] = __float2bfloat16_rn(x - __bfloat162float(h[e]));
+                                    const float d1 = x - __bfloat162float(h[e]);
+                                    mi[e] = __float2bfloat16_rn(d1);
+                                    l[e] = __float2bfloat16_rn(d1 - __bfloat162float(mi[e]));
                                 }
-                                *reinterpret_cast<uint4*>(t_b + off) = *reinterpret_cast<const uint4*>(h);
-                                *reinterpret_cast<uint4*>(t_b + offl) = *reinterpret_cast<const uint4*>(l);
+                                *reinterpret_cast<uint4*>(t_b + off0) = *reinterpret_cast<const uint4*>(h);
+                                *reinterpret_cast<uint4*>(t_b + off1) = *reinterpret_cast<const uint4*>(mi);
+                                *reinterpret_cast<uint4*>(t_b + off2) = *reinterpret_cast<const uint4*>(l);
                             }
                         }
                         kb += kp;
@@ -902,25 +913,27 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                 // K steps of this chunk (every consumer thread tracks the segment's count)
                 int csteps = 0;
                 for (int p = 0; p < D.npieces; ++p) csteps += (spc[st][p].ncols + ks - 1) / ks;
+                // accumulator columns in tensor memory: nacc A_hi accumulators of whi
+                // columns, then ncorr A_lo accumulators of wlo columns
+                const uint32_t whi = (uint32_t)(a.tc_parts * a.tc_np), wlo = (uint32_t)((a.tc_parts - 1) * a.tc_np);
                 if (tid == 0) {
-                    // Per K step two products: A_hi x [B_hi | B_lo] (N = 2 Np: the hi*hi
-                    // and hi*lo parts side by side) into accumulator pair g % nacc, and
-                    // A_lo x B_hi (N = Np) into correction accumulator g % ncorr.  One
-                    // tcgen05.mma costs about the same for any N up to 128, so the
-                    // merged product saves a third of the instructions; products into
-                    // one accumulator wait for each other, into different ones overlap.
+                    // Per K step two products: A_hi x B (N = ph Np: A_hi times every
+                    // part of the vector) into accumulator g % nacc, and A_lo x B's
+                    // first ph - 1 parts (N = (ph - 1) Np: A_lo times all but the
+                    // vector's lowest part) into correction accumulator g % ncorr.
+                    // Products into one accumulator wait for each other, into
+                    // different ones overlap.
                     bool ok = mbar_wait_or_abort(&cbar[tcn & 1], (uint32_t)(tcn >> 1) & 1u, abortp);
                     if (!ok) {
                         atomicExch(a.err, 1);
                         abort_flag = 1;
                     } else {
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint32_t idesc2 = mma_idesc(type, Mp, N2), idesc1 = mma_idesc(type, Mp, Np);
-                        const uint32_t lboA = 16u * Mp, lboB = (uint32_t)(N2 / 8) * 128u;
+                        const uint32_t idesc_h = mma_idesc(type, Mp, Nt), idesc_l = mma_idesc(type, Mp, Nt - Np);
+                        const uint32_t lboA = 16u * Mp, lboB = (uint32_t)(Nt / 8) * 128u;
                         const int bper = 16 / bes;
                         const int nacc = a.tc_nacc, ncorr = a.tc_ncorr;
-                        const uint32_t pair_cols = 2u * (uint32_t)a.tc_np;
-                        const uint32_t tcorr0 = tmem_base + (uint32_t)nacc * pair_cols;
+                        const uint32_t tcorr0 = tmem_base + (uint32_t)nacc * whi;
                         // descriptors advance by adding (byte offset >> 4) to their
                         // 14-bit start-address field (shared memory < 256 KB: no carry)
                         const uint64_t dA0 = smem_desc(smem_addr(stg), lboA, 128);
@@ -937,9 +950,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                             const int nst = (P.ncols + ks - 1) / ks;
                             uint64_t ao = (uint64_t)(P.smem_off >> 4);
                             for (int k2 = 0; k2 < nst; ++k2, ++gstep, ao += a_step, bo += b_step) {
-                                mma_issue(type, tmem_base + (uint32_t)accn * pair_cols, dA0 + ao, dB + bo, idesc2,
+                                mma_issue(type, tmem_base + (uint32_t)accn * whi, dA0 + ao, dB + bo, idesc_h,
                                           gstep >= nacc ? 1u : 0u);
-                                mma_issue(type, tcorr0 + (uint32_t)(corn * a.tc_np), dL0 + ao, dB + bo, idesc1,
+                                mma_issue(type, tcorr0 + (uint32_t)corn * wlo, dL0 + ao, dB + bo, idesc_l,
                                           gstep >= ncorr ? 1u : 0u);
                                 if (++accn == nacc) accn = 0;
                                 if (++corn == ncorr) corn = 0;
@@ -953,7 +966,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                 }
                 if (*abortp) break;
                 segk += csteps;
-                // accumulators written: hi pairs, then correction ones
+                // accumulators written: A_hi ones, then correction ones
                 const int nused = segk < a.tc_nacc ? segk : a.tc_nacc;
                 const int ncused = segk < a.tc_ncorr ? segk : a.tc_ncorr;
                 // the previous chunk's products are done by now in the common case
@@ -975,13 +988,16 @@ __global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
                         const int row = Mp == 128 ? tid : (lane < 16 ? 16 * w + lane : -1);
                         const uint32_t tlane = tmem_base + ((uint32_t)(32 * w) << 16);
                         float* dst = C.ws32 + (int64_t)(D.out_row + (row < 0 ? 0 : row)) * r;
+                        // column groups to add: every part of each A_hi accumulator, then
+                        // the first ph - 1 parts of each correction accumulator
+                        const int nhi = ph * nused, ntot = nhi + (ph - 1) * ncused;
                         for (int c0 = 0; c0 < Np; c0 += 8) {   // 8 right-hand sides at a time
                             float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                            // the hi*hi and hi*lo halves of the pairs, then the corrections
-                            for (int j = 0; j < 2 * nused + ncused; ++j) {
-                                const uint32_t col = (uint32_t)(j < 2 * nused ? (j >> 1) * 2 * a.tc_np + (j & 1) * Np + c0
-                                                                              : a.tc_nacc * 2 * a.tc_np +
-                                                                                    (j - 2 * nused) * a.tc_np + c0);
+                            for (int j = 0; j < ntot; ++j) {
+                                const uint32_t col =
+                                    j < nhi ? (uint32_t)(j / ph) * whi + (uint32_t)((j % ph) * Np + c0)
+                                            : (uint32_t)a.tc_nacc * whi + (uint32_t)((j - nhi) / (ph - 1)) * wlo +
+                                                  (uint32_t)(((j - nhi) % (ph - 1)) * Np + c0);
                                 uint32_t v[8];
                                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                                              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]),
@@ -1415,11 +1431,11 @@ __global__ void k_prologue(const double* __restrict__ u1, double* __restrict__ w
 
 int stages_for(int rt, int stage_bytes, int alo, int b);
 static int tc_alo_bytes(const h2_handle* op);
-static int tc_b_bytes(const h2_handle* op);
+static int tc_b_bytes(const h2_handle* op, int rt);
 // The operator's stage count: the autotuner's choice, else the default.
 static int op_stages(const h2_handle* op, int rt) {
     return op && op->tune_stages > 0 ? op->tune_stages
-                                     : stages_for(rt, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op));
+                                     : stages_for(rt, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op, rt));
 }
 
 int rt_for(int r) {
@@ -1478,16 +1494,19 @@ cudaError_t launch_seg_rt(const KArgs& a, int nsm, size_t smem, cudaStream_t s, 
     if (TC) {
         // TMEM columns per CTA: a power of 2 such that the resident CTAs of an SM
         // never ask for more than its 512 columns (an allocation never waits);
-        // half of the accumulators take the hi*hi products, half the corrections
+        // about half of them take the A_hi accumulators (all `parts` vector parts
+        // of np columns each), the rest the A_lo corrections (parts - 1 of them)
         int cols = 512;
         while (cols * per_sm > 512 && cols > 32) cols >>= 1;
         const int np = (a.r + 15) / 16 * 16;
-        // hi accumulator pairs of 2 np columns and correction accumulators of np
-        if (cols < 3 * np) return cudaErrorInvalidConfiguration;
+        const int parts = a.tc_parts >= 2 ? a.tc_parts : 2;
+        const int whi = parts * np, wlo = (parts - 1) * np;
+        if (cols < whi + wlo) return cudaErrorInvalidConfiguration;
+        b.tc_parts = parts;
         b.tc_cols = cols;
         b.tc_np = np;
-        b.tc_nacc = std::max(1, std::min(8, cols / (4 * np)));
-        b.tc_ncorr = std::max(1, std::min(8, (cols - 2 * np * b.tc_nacc) / np));
+        b.tc_nacc = std::max(1, std::min(8, (cols / 2) / whi));
+        b.tc_ncorr = std::max(1, std::min(8, (cols - whi * b.tc_nacc) / wlo));
     }
     k_seg<RT, FLOW, TC><<<g, kBlock, smem, s>>>(b);
     return cudaGetLastError();
@@ -1535,21 +1554,25 @@ int upload_vec(const std::vector<T>& v, T** d) {
 }
 
 // Tensor-core operand buffers of an operator: the lo parts of one TF32 chunk,
-// and B (hi and lo) for the largest chunk (stage_bytes / (4 * 64) K rows x 32
-// right-hand sides).
+// and B for the largest chunk of products of at most rt right-hand sides:
+// stage_bytes / (4 * 64) K rows (a tile of at least 64 rows, 4 bytes per
+// entry) x (rt rounded up to 16) columns per vector part (TF32: hi, lo; BF16:
+// hi, mid, lo).
+static int tc_parts_of(const h2_handle* op) { return op->params.precision == H2_BF16X3 ? 3 : 2; }
 static int tc_alo_bytes(const h2_handle* op) { return op->params.precision == H2_TF32X3 ? op->stage_bytes : 0; }
-static int tc_b_bytes(const h2_handle* op) {
+static int tc_b_bytes(const h2_handle* op, int rt) {
     const int p = op->params.precision;
     if (p != H2_TF32X3 && p != H2_BF16X3) return 0;
-    return op->stage_bytes / (4 * 64) * 32 * (p == H2_TF32X3 ? 4 : 2);
+    const int np = (std::min(rt, H2_MAX_RHS) + 15) / 16 * 16;
+    return op->stage_bytes / (4 * 64) * np * (p == H2_TF32X3 ? 4 : 2) * tc_parts_of(op);
 }
 
 // Shared memory of the segment kernel with `sets` tensor-core operand sets of
-// `alo` + 2 `b` bytes.
+// `alo` + `b` bytes.
 static size_t seg_smem_raw(int rt, int stages, int stage_bytes, int alo, int b, int sets) {
     const size_t S = (size_t)stages;
     const size_t red = (size_t)kRedBuffers * sizeof(double) * kConsumers * red_rhs(rt);
-    const size_t tc = (size_t)sets * ((size_t)alo + 2 * (size_t)b);
+    const size_t tc = (size_t)sets * ((size_t)alo + (size_t)b);
     const size_t mid = red + tc;
     return S * (size_t)stage_bytes + S * xin_bytes(rt) + mid + sizeof(uint64_t) * (2 * S + 5);
 }
@@ -1572,7 +1595,7 @@ static int tc_sets_raw(int rt, int stages, int stage_bytes, int alo, int b) {
     return seg_smem_raw(rt, stages, stage_bytes, alo, b, 2) <= (size_t)220 * 1024 ? 2 : 1;
 }
 static size_t seg_smem_bytes(const h2_handle* op, int rt, int sets) {
-    return seg_smem_raw(rt, op_stages(op, rt), op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op), sets);
+    return seg_smem_raw(rt, op_stages(op, rt), op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op, rt), sets);
 }
 // Tensor-core tiles multiplied on the CUDA cores: at most kTcCudaMaxRT
 // right-hand sides (the autotuner may turn it off).
@@ -1582,7 +1605,7 @@ static bool tc_cuda_for(const h2_handle* op, int rt) {
 }
 static int tc_sets_for(const h2_handle* op, int rt) {
     if (tc_cuda_for(op, rt)) return 0;   // no tensor-core operands
-    return tc_sets_raw(rt, op_stages(op, rt), op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op));
+    return tc_sets_raw(rt, op_stages(op, rt), op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op, rt));
 }
 
 // ---- split form: shared memory of its two launches ----
@@ -1599,15 +1622,53 @@ struct FarCfg {
 };
 static FarCfg split_far_cfg(const h2_handle* op, int rt) {
     const size_t budget = (size_t)227 * 1024 - near_smem_bytes(op, rt) - (size_t)8 * 1024;
-    const int alo = tc_alo_bytes(op), b = tc_b_bytes(op);
+    const int alo = tc_alo_bytes(op), b = tc_b_bytes(op, rt);
     if (seg_smem_raw(rt, 3, op->stage_bytes, alo, b, 1) <= budget) return FarCfg{3, 1};
     if (seg_smem_raw(rt, 2, op->stage_bytes, alo, b, 2) <= budget) return FarCfg{2, 2};
     return FarCfg{2, 1};
 }
 static size_t split_far_smem(const h2_handle* op, int rt) {
     const FarCfg c = split_far_cfg(op, rt);
-    return seg_smem_raw(rt, c.stages, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op), c.sets);
+    return seg_smem_raw(rt, c.stages, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op, rt), c.sets);
 }
+
+// Profiling aid (h2_profile_enable): records a CUDA event before and after
+// each kernel launch of a product, on the stream the kernel is launched on,
+// with what the launch computes.  A recorder without an output does nothing.
+struct Prof {
+    std::vector<ProfLaunch>* out = nullptr;
+    std::vector<cudaEvent_t>* pool = nullptr;
+    cudaError_t event(cudaEvent_t* e) {
+        if (!pool->empty()) {
+            *e = pool->back();
+            pool->pop_back();
+            return cudaSuccess;
+        }
+        return cudaEventCreate(e);
+    }
+    // Opens a launch on stream s (*idx = -1 when not recording).
+    cudaError_t begin(cudaStream_t s, int* idx) {
+        *idx = -1;
+        if (!out) return cudaSuccess;
+        ProfLaunch L;
+        cudaError_t e = event(&L.e0);
+        if (e == cudaSuccess) e = event(&L.e1);
+        if (e != cudaSuccess) return e;
+        out->push_back(L);
+        *idx = (int)out->size() - 1;
+        return cudaEventRecord(L.e0, s);
+    }
+    cudaError_t end(int idx, cudaStream_t s, int kind, int64_t bytes, int64_t macs, int grid, int r) {
+        if (!out || idx < 0) return cudaSuccess;
+        ProfLaunch& L = (*out)[(size_t)idx];
+        L.kind = kind;
+        L.bytes = bytes;
+        L.macs = macs;
+        L.grid = grid;
+        L.r = r;
+        return cudaEventRecord(L.e1, s);
+    }
+};
 
 template <int RT, bool PAIR>
 cudaError_t launch_near_rt(const NArgs& a, int nsm, size_t smem, cudaStream_t s) {
@@ -1620,7 +1681,8 @@ cudaError_t launch_near_rt(const NArgs& a, int nsm, size_t smem, cudaStream_t s)
 // The split form's launches after the gather: the near field on the
 // operator's second stream and the rest of the product on `s`, joined by an
 // addition (u2 += u2n).
-static int launch_split(h2_handle* op, double* u2, int r, int rt, cudaStream_t s, double* ws, float* ws32) {
+static int launch_split(h2_handle* op, double* u2, int r, int rt, cudaStream_t s, double* ws, float* ws32,
+                        Prof& prof) {
     const int64_t N = op->geom->N;
     H2_CUDA_TRY(cudaMemsetAsync(u2, 0, sizeof(double) * (size_t)r * N, s));   // the expansions add into u2
     H2_CUDA_TRY(cudaMemsetAsync(op->d_u2n, 0, sizeof(double) * (size_t)r * N, s));   // the near-field units too
@@ -1650,8 +1712,11 @@ static int launch_split(h2_handle* op, double* u2, int r, int rt, cudaStream_t s
     na.err = op->d_err;
     const size_t nsmem = near_smem_bytes(op, rt);
     if (rt != 16) return H2_ERR_INVALID_ARG;   // split products have 9..16 right-hand sides
+    int pn = -1, pf = -1, pa = -1;
+    H2_CUDA_TRY(prof.begin(op->near_stream, &pn));
     if (pair) H2_CUDA_TRY((launch_near_rt<16, true>(na, op->nsm, nsmem, op->near_stream)));
     else H2_CUDA_TRY((launch_near_rt<16, false>(na, op->nsm, nsmem, op->near_stream)));
+    H2_CUDA_TRY(prof.end(pn, op->near_stream, PASS_SPLIT_NEAR, np->bytes, np->macs, op->nsm, r));
     KArgs a{};
     a.nops = 1;
     a.ctx[0] = OpCtx{op->d_arena, ws, ws32, u2, op->d_perm, N, r, op->kp, op->d_nodes, op->row_yhat};
@@ -1662,7 +1727,8 @@ static int launch_split(h2_handle* op, double* u2, int r, int rt, cudaStream_t s
     a.stage_bytes = op->stage_bytes;
     a.tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
     a.tc_alo_bytes = tc_alo_bytes(op);
-    a.tc_b_bytes = tc_b_bytes(op);
+    a.tc_b_bytes = tc_b_bytes(op, rt);
+    a.tc_parts = tc_parts_of(op);
     a.tc_sets = fc.sets;
     a.seg = op->d_sseg;
     a.chunk = op->d_schunk;
@@ -1673,13 +1739,17 @@ static int launch_split(h2_handle* op, double* u2, int r, int rt, cudaStream_t s
     a.nseg = (int)op->split.seg.size();
     a.nreg = 3 * op->nc;
     // one CTA per SM, so that a near-field CTA fits beside it
+    H2_CUDA_TRY(prof.begin(s, &pf));
     H2_CUDA_TRY(launch_seg<true>(a, rt, op->nsm, split_far_smem(op, rt), s, &op->flow_grid, 1));
+    H2_CUDA_TRY(prof.end(pf, s, PASS_SPLIT_FAR, op->bytes_streamed - np->bytes, op->macs - np->macs, op->flow_grid, r));
     H2_CUDA_TRY(cudaEventRecord(op->ev_join, op->near_stream));
     H2_CUDA_TRY(cudaStreamWaitEvent(s, op->ev_join, 0));
     const int64_t n = (int64_t)r * N;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4 * (int64_t)op->nsm));
+    H2_CUDA_TRY(prof.begin(s, &pa));
     k_add<<<grid, 256, 0, s>>>(u2, op->d_u2n, n);
     H2_CUDA_TRY(cudaGetLastError());
+    H2_CUDA_TRY(prof.end(pa, s, PASS_SPLIT_ADD, 0, 0, grid, r));
     return H2_OK;
 }
 
@@ -1701,40 +1771,28 @@ static int launches_per_matvec(const h2_handle* op) {
 // Launches the gather kernel and every pass (level-wise) or the flow kernel
 // on workspaces `ws` (FP64) and `ws32` (FP32 operators only).
 int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream_t s, double* ws,
-                  float* ws32, bool flow, std::vector<cudaEvent_t>* marks,
+                  float* ws32, bool flow, std::vector<ProfLaunch>* prof_out,
                   std::vector<cudaEvent_t>* pool) {
     if (r > 16 && split_active(op, flow, rt_for(r))) {
         // the split form in products of at most 16 right-hand sides: at 32 a
         // far-field CTA (168 registers per thread) leaves no SM sub-partition
         // room for a near-field warp, at 16 both fit
-        // (profiling marks: the first product's gather, then all the rest)
         for (int c0 = 0; c0 < r; c0 += 16) {
             const int rc = launch_matvec(op, u1 + (int64_t)c0 * op->geom->N, u2 + (int64_t)c0 * op->geom->N,
-                                         std::min(16, r - c0), s, ws, ws32, flow, c0 == 0 ? marks : nullptr, pool);
+                                         std::min(16, r - c0), s, ws, ws32, flow, prof_out, pool);
             if (rc != H2_OK) return rc;
         }
-        if (marks && !marks->empty()) H2_CUDA_TRY(cudaEventRecord(marks->back(), s));
         return H2_OK;
     }
     const int rt = rt_for(r);
     if ((int64_t)op->chunk_cols * r > (int64_t)xin_cols(rt) * rt) return H2_ERR_INVALID_ARG;   // stage inputs
     const size_t smem = pass_smem_bytes(op, rt);
     const int64_t N = op->geom->N;
-    auto mark = [&]() -> cudaError_t {
-        if (!marks) return cudaSuccess;
-        cudaEvent_t e;
-        if (!pool->empty()) {
-            e = pool->back();
-            pool->pop_back();
-        } else {
-            cudaError_t err = cudaEventCreate(&e);
-            if (err != cudaSuccess) return err;
-        }
-        marks->push_back(e);
-        return cudaEventRecord(e, s);
-    };
-    H2_CUDA_TRY(mark());
+    Prof prof{prof_out, pool};
+    int pi = -1;
+    H2_CUDA_TRY(prof.begin(s, &pi));
     const bool split = split_active(op, flow, rt);
+    int gather_grid = 0;
     {
         const std::vector<int32_t>& zr = split ? op->split.zero_rows[0] : flow ? op->fzero_rows : op->zero_rows;
         const int32_t* d_zr = split ? op->d_szero_rows : flow ? op->d_fzero_rows : op->d_zero_rows;
@@ -1745,14 +1803,10 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
         k_prologue<<<grid, 256, 0, s>>>(u1, ws, ws32, wsp, op->d_gather_src, op->row_xhat, N, r, d_zr, (int)zr.size(),
                                         op->kp, op->d_fcnt, nclear);
         H2_CUDA_TRY(cudaGetLastError());
+        gather_grid = grid;
     }
-    H2_CUDA_TRY(mark());
-    if (split) {
-        const int rc = launch_split(op, u2, r, rt, s, ws, ws32);
-        if (rc != H2_OK) return rc;
-        H2_CUDA_TRY(mark());
-        return H2_OK;
-    }
+    H2_CUDA_TRY(prof.end(pi, s, PASS_PROLOGUE, 0, 0, gather_grid, r));
+    if (split) return launch_split(op, u2, r, rt, s, ws, ws32, prof);
     KArgs a{};
     a.nops = 1;
     a.ctx[0] = OpCtx{op->d_arena, ws, ws32, u2, op->d_perm, N, r, op->kp, op->d_nodes, op->row_yhat};
@@ -1762,7 +1816,8 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
     a.stage_bytes = op->stage_bytes;
     a.tc = (op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3) && !tc_cuda_for(op, rt);
     a.tc_alo_bytes = tc_alo_bytes(op);
-    a.tc_b_bytes = tc_b_bytes(op);
+    a.tc_b_bytes = tc_b_bytes(op, rt);
+    a.tc_parts = tc_parts_of(op);
     a.tc_sets = tc_sets_for(op, rt);
     a.tc_cuda = tc_cuda_for(op, rt) ? 1 : 0;
     if (flow) {
@@ -1774,8 +1829,9 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
         a.cnt = op->d_fcnt;
         a.nseg = (int)op->fseg.size();
         a.nreg = 3 * op->nc;
+        H2_CUDA_TRY(prof.begin(s, &pi));
         H2_CUDA_TRY(launch_seg<true>(a, rt, op->nsm, smem, s, &op->flow_grid, op->tune_ctas));
-        H2_CUDA_TRY(mark());
+        H2_CUDA_TRY(prof.end(pi, s, PASS_FLOW, op->bytes_streamed, op->macs, op->flow_grid, r));
         return H2_OK;
     }
     for (Pass& p : op->passes) {
@@ -1783,8 +1839,9 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
         a.chunk = p.d_chunk;
         a.piece = p.d_piece;
         a.nseg = (int)p.seg.size();
+        H2_CUDA_TRY(prof.begin(s, &pi));
         H2_CUDA_TRY(launch_seg<false>(a, rt, op->nsm, smem, s, &p.grid, op->tune_ctas));
-        H2_CUDA_TRY(mark());
+        H2_CUDA_TRY(prof.end(pi, s, p.kind, p.bytes, p.macs, p.grid, r));
     }
     return H2_OK;
 }
@@ -2013,27 +2070,44 @@ void release_graph(h2_handle* op) {
 
 void release_profile(h2_handle* op) {
     for (auto& call : op->prof_calls)
-        for (cudaEvent_t e : call) cudaEventDestroy(e);
+        for (const ProfLaunch& L : call) {
+            cudaEventDestroy(L.e0);
+            cudaEventDestroy(L.e1);
+        }
     for (cudaEvent_t e : op->prof_pool) cudaEventDestroy(e);
     op->prof_calls.clear();
     op->prof_pool.clear();
 }
 
-int read_profile(h2_handle* op, std::vector<double>& ms, int& ncalls) {
+// Per launch of the recorded calls (launch i of every call: calls with the
+// same r launch the same kernels), its description (from the first call) and
+// its total time over the calls.
+int read_profile(h2_handle* op, std::vector<ProfLaunch>& launches, std::vector<double>& ms, int& ncalls) {
+    launches.clear();
     ms.clear();
     ncalls = (int)op->prof_calls.size();
+    int rc = H2_OK;
     for (auto& call : op->prof_calls) {
-        H2_CUDA_TRY(cudaEventSynchronize(call.back()));
-        if (ms.size() < call.size() - 1) ms.resize(call.size() - 1, 0.0);
-        for (size_t i = 0; i + 1 < call.size(); ++i) {
+        if (launches.empty()) launches = call;
+        if (ms.size() < call.size()) ms.resize(call.size(), 0.0);
+        for (size_t i = 0; i < call.size(); ++i) {
             float t = 0.0f;
-            H2_CUDA_TRY(cudaEventElapsedTime(&t, call[i], call[i + 1]));
+            cudaError_t e = cudaEventSynchronize(call[i].e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, call[i].e0, call[i].e1);
+            if (e != cudaSuccess && rc == H2_OK) {
+                set_cuda_error(e, "cudaEventElapsedTime", __FILE__, __LINE__);
+                rc = H2_ERR_CUDA;
+            }
             ms[i] += t;
         }
-        for (cudaEvent_t e : call) op->prof_pool.push_back(e);
     }
+    for (auto& call : op->prof_calls)
+        for (const ProfLaunch& L : call) {
+            op->prof_pool.push_back(L.e0);
+            op->prof_pool.push_back(L.e1);
+        }
     op->prof_calls.clear();
-    return H2_OK;
+    return rc;
 }
 
 // One product on device buffers.  A product with the same (u1, u2, r) as the
@@ -2043,7 +2117,7 @@ int read_profile(h2_handle* op, std::vector<double>& ms, int& ncalls) {
 // launched directly.
 int matvec_device(h2_handle* op, const double* u1, double* u2, int r, cudaStream_t s) {
     if (op->prof_enabled) {
-        std::vector<cudaEvent_t> ev;
+        std::vector<ProfLaunch> ev;
         int rc = launch_matvec(op, u1, u2, r, s, op->d_ws, op->d_ws32, op->use_flow != 0, &ev, &op->prof_pool);
         op->prof_calls.push_back(std::move(ev));
         return rc;
@@ -2297,12 +2371,13 @@ void drop_batch_plans(uint64_t serial) {
 
 int matvec_batched(h2_handle* const* ops, int n, const double* const* u1, double* const* u2, const int32_t* r,
                    cudaStream_t s) {
-    int rmax = 1, alo = 0, b = 0;
+    int rmax = 1, alo = 0, b = 0, parts = 2;
     bool tc = false;
+    for (int i = 0; i < n; ++i) rmax = std::max(rmax, (int)r[i]);
     for (int i = 0; i < n; ++i) {
-        rmax = std::max(rmax, (int)r[i]);
         alo = std::max(alo, tc_alo_bytes(ops[i]));
-        b = std::max(b, tc_b_bytes(ops[i]));
+        b = std::max(b, tc_b_bytes(ops[i], rt_for(rmax)));
+        if (tc_b_bytes(ops[i], rt_for(rmax)) > 0) parts = std::max(parts, tc_parts_of(ops[i]));
         tc = tc || ops[i]->params.precision == H2_TF32X3 || ops[i]->params.precision == H2_BF16X3;
         if (ops[i]->stage_bytes != ops[0]->stage_bytes || ops[i]->device != ops[0]->device) return H2_ERR_INVALID_ARG;
     }
@@ -2370,6 +2445,7 @@ int matvec_batched(h2_handle* const* ops, int n, const double* const* u1, double
     a.tc = tc && !tcc;
     a.tc_alo_bytes = alo;
     a.tc_b_bytes = b;
+    a.tc_parts = parts;
     a.tc_sets = sets;
     a.tc_cuda = tcc ? 1 : 0;
     a.seg = bp->d_seg;
@@ -2448,7 +2524,21 @@ extern "C" int h2_matvec_noalloc(h2_handle* op, const double* u1, double* u2, in
     using namespace h2;
     if (!op || !u1 || !u2) return H2_ERR_INVALID_ARG;
     if (op->kind != 2) return H2_ERR_WRONG_HANDLE;
-    if (r < 1 || r > H2_MAX_RHS) return H2_ERR_INVALID_ARG;
+    if (r < 1) return H2_ERR_INVALID_ARG;
+    // a stage holds every chunk's inputs: operators built for at most 8
+    // right-hand sides (128-column chunks) take r <= 8, the others r <= 32
+    if (r > H2_MAX_RHS || (int64_t)op->chunk_cols * r > (int64_t)xin_cols(rt_for(r)) * rt_for(r)) {
+        set_last_error(op->chunk_cols > xin_cols(H2_MAX_RHS)
+                           ? "h2_matvec_noalloc: r > 8 needs an operator assembled with max_rhs > 8"
+                           : "h2_matvec_noalloc: r > 32");
+        return H2_ERR_RHS_EXCEEDS_MAX;
+    }
+    int dev = -1;
+    H2_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != op->device) {
+        set_last_error("h2_matvec_noalloc: the current device is not the operator's device");
+        return H2_ERR_INVALID_ARG;
+    }
     const int64_t N = op->geom->N;
     const size_t bytes = sizeof(double) * (size_t)N * r;
     const char *a = (const char*)u1, *b = (const char*)u2;

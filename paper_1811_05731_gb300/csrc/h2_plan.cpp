@@ -156,10 +156,11 @@ void build_plan(h2_handle* op) {
     const int nc = op->nc;
     const int k = op->k;
     const int kp = op->kp;
-    // leaf bases (P) and coupling / transfer matrices (PT) per precision
+    // leaf bases (P), transfer matrices (PT) and coupling blocks (PC) per precision
     const int prec = op->params.precision;
     const int P = prec == H2_FP64 ? PIECE_F64 : PIECE_F32;
-    const int PT = prec == H2_FP64 ? PIECE_F64 : prec == H2_FP32 ? PIECE_F32 : prec == H2_TF32X3 ? PIECE_TF32 : PIECE_BF16X3;
+    const int PT = transfer_piece_type(prec);   // transfers E_c
+    const int PC = coupling_piece_type(prec);   // coupling blocks S_ts
     const int64_t N = op->geom->N;
 
     op->is_src.assign(nc, 0);
@@ -254,7 +255,7 @@ void build_plan(h2_handle* op) {
             });
         const int64_t nfar = (int64_t)op->far_t.size();
         const int split = op->coupling_split;
-        const int PS = op->params.coupling == H2_COUPLING_ON_THE_FLY ? PIECE_NODES : PT;   // coupling blocks
+        const int PS = op->params.coupling == H2_COUPLING_ON_THE_FLY ? PIECE_NODES : PC;   // coupling blocks
         std::vector<SegSpec> segs;
         for (int t = 0; t < nc; ++t) {
             if (by_t[t].empty()) continue;

@@ -12,8 +12,17 @@ import synth  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
+# The max-norm error is held to twice the tolerance: a rounding error spread
+# over the rows peaks at a few times its root mean square, while an error
+# confined to one leaf or block at ten times the budget still fails.
+MAXNORM_FACTOR = 2.0
+
+
 def rel_err(y, ref):
-    return np.linalg.norm(y - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+    """The larger of the relative L2 and the relative max-norm error per right-hand side."""
+    l2 = np.linalg.norm(y - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+    mx = np.max(np.abs(y - ref), axis=-1) / np.max(np.abs(ref), axis=-1)
+    return np.maximum(l2, mx / MAXNORM_FACTOR)
 
 
 def _small_set():
@@ -41,7 +50,7 @@ def test_batched_small_meshes_match_oracle_and_single_products():
         assert pkg.h2_device_status(ops[0].handle) == 0
         for (mesh, m, leaf, prec, r), y, ref, single in zip(items, ys, refs, singles):
             y = y.cpu().numpy()
-            tol = 1e-8 if prec == pkg.FP64 else (1e-4 if prec == pkg.BF16X3 else 1e-5)
+            tol = 1e-8 if prec == pkg.FP64 else (2e-5 if prec == pkg.BF16X3 else 1e-5)
             assert np.all(rel_err(y, ref) <= tol), (prec, rel_err(y, ref))
             # same segments and arithmetic, only the order of atomic additions
             # differs -- except for tensor-core tiles, which the batched launch
@@ -53,21 +62,45 @@ def test_batched_small_meshes_match_oracle_and_single_products():
                 assert np.all(rel_err(y, single) <= (1e-13 if prec == pkg.FP64 else 1e-6)), (prec, rel_err(y, single))
 
 
+def _leaf_rows(o, n_leaves):
+    """Every node of `n_leaves` leaves spread evenly over the tree order."""
+    tr = o.tree()
+    leaves = [c for c in range(len(tr["size"])) if tr["child0"][c] < 0]
+    pick = sorted({leaves[int(i)] for i in np.linspace(0, len(leaves) - 1, n_leaves)})
+    return np.concatenate([tr["perm"][tr["start"][c]:tr["start"][c] + tr["size"][c]] for c in pick])
+
+
 def test_batched_eight_uneven_meshes():
-    """The eight meshes of 5k-100k nodes (m = 5, leaf 64) in one launch, FP64 and BF16 hi+lo."""
+    """The eight meshes of 5k-100k nodes (m = 5, leaf 64, eta = 2) in one launch,
+    FP64, FP32 and BF16 hi+lo: every mesh's result against the oracle's H2
+    product on sampled rows (all nodes of 4 leaves spread over its tree; 1e-8
+    FP64, 1e-5 FP32, 2e-5 BF16 hi + lo) and against the same operator's single
+    product."""
     meshes = synth.workloads.multi_mesh_set()
-    for prec, tol in ((pkg.FP64, 1e-12), (pkg.BF16X3, 1e-6)):
+    xs_np = [synth.smooth_states(mesh, 1, 1811 + i) for i, mesh in enumerate(meshes)]
+    rows, refs = [], []
+    for mesh, x in zip(meshes, xs_np):
+        o = oracle.H2Oracle(mesh.xyz, mesh.tri, 5, 64, 2.0, store=False)
+        rows.append(_leaf_rows(o, 4))
+        refs.append(o.rows(x, rows[-1]))
+        o.close()
+    # BF16 hi + lo: its fixed budget 2e-5 from the 17-bit coupling storage (test_gpu_parity)
+    for prec, tol_single, tol_oracle in ((pkg.FP64, 1e-12, 1e-8), (pkg.FP32, 1e-6, 1e-5),
+                                         (pkg.BF16X3, 1e-6, 2e-5)):
         ops, xs = [], []
-        for i, mesh in enumerate(meshes):
+        for mesh, x in zip(meshes, xs_np):
             g = pkg.Geometry(mesh.xyz, mesh.tri)
             ops.append(pkg.Operator(g, m=5, leaf=64, precision=prec, max_rhs=1))
-            xs.append(torch.from_numpy(synth.smooth_states(mesh, 1, 1811 + i)).cuda())
+            xs.append(torch.from_numpy(x).cuda())
         singles = [op.matvec(x).cpu().numpy() for op, x in zip(ops, xs)]
-        ys = pkg.matvec_batched(ops, xs)
+        ys = pkg.matvec_batched(ops, xs, [torch.full_like(x, float("nan")) for x in xs])
         torch.cuda.synchronize()
         assert pkg.h2_device_status(ops[0].handle) == 0
-        for y, single in zip(ys, singles):
-            assert np.all(rel_err(y.cpu().numpy(), single) <= tol)
+        for i, (y, single) in enumerate(zip(ys, singles)):
+            y = y.cpu().numpy()
+            assert np.all(rel_err(y, single) <= tol_single), (prec, i, rel_err(y, single))
+            e = rel_err(y[:, rows[i]], refs[i])
+            assert np.all(e <= tol_oracle), (prec, i, e)
         del ops
 
 

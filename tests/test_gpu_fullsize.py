@@ -4,8 +4,10 @@ The CPU oracle computes selected rows of the H2 product exactly as its
 definition states (direct Chebyshev bases on every cluster's own box, exact
 Lindholm near entries, the solid-angle diagonal), one row at a time; the GPU
 computes the whole product in the launch configuration the benchmark times
-(dataflow schedule).  The rows are every node of two leaves (the first and a
-middle one of the tree), so that every level of the block tree contributes.
+(dataflow schedule).  The rows are every node of 16 leaves spread evenly over
+the tree order (about 1,000 rows), so that every level of the block tree and
+every region of the surface contributes; each comparison bounds both the
+relative L2 error and the relative max-norm error over the sampled rows.
 
 Workloads (synth.workloads): the 1000 x 1000 x 10 film (209,922 nodes, m = 5),
 the 3:2:1 ellipsoid with 32 smooth right-hand sides (163,842 nodes, m = 5) and
@@ -23,20 +25,34 @@ import synth  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-8
-TOL = {"fp64": FP64_TOL, "fp32": 1e-5, "tf32x3": 1e-5, "fp32-onfly": 1e-5}
-# BF16 hi + lo stores about 17 significant bits (|a - hi - lo| <= 2^-17 |a|
-# with round-to-nearest hi and lo) against FP32's 24: its error is the FP32
-# form's error (the workload's amplification of per-entry rounding, measured
-# on the same rows) scaled by 2^(24 - 17), with a factor 2 of margin.
-BF16_OVER_FP32 = 2.0 * 2.0 ** (24 - 17)
+MIXED_TOL = 1e-5
+# BF16 hi + lo: a fixed budget from its 17-bit coupling storage (2^-18 per
+# entry, amplified 3-10 times by the far-field sums), see test_gpu_parity
+BF16_TOL = 2e-5
+TOL = {"fp64": FP64_TOL, "fp32": MIXED_TOL, "tf32x3": MIXED_TOL, "bf16x3": BF16_TOL, "fp32-onfly": MIXED_TOL}
 PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3, "fp32-onfly": 1}
+N_LEAVES = 16
 
 
-def sampled_rows(o):
+def sampled_rows(o, n_leaves=N_LEAVES):
+    """Every node of `n_leaves` leaves spread evenly over the tree order."""
     tr = o.tree()
     leaves = [c for c in range(len(tr["size"])) if tr["child0"][c] < 0]
-    pick = [leaves[0], leaves[len(leaves) // 2]]
+    pick = sorted({leaves[int(i)] for i in np.linspace(0, len(leaves) - 1, n_leaves)})
     return np.concatenate([tr["perm"][tr["start"][c]:tr["start"][c] + tr["size"][c]] for c in pick])
+
+
+# The max-norm error is held to twice the tolerance: a rounding error spread
+# over the rows peaks at a few times its root mean square, while an error
+# confined to one leaf or block at ten times the budget still fails.
+MAXNORM_FACTOR = 2.0
+
+
+def rel_err(y, ref):
+    """Per right-hand side, the larger of the relative L2 and max-norm errors."""
+    l2 = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    mx = np.max(np.abs(y - ref), axis=1) / np.max(np.abs(ref), axis=1)
+    return np.maximum(l2, mx / MAXNORM_FACTOR)
 
 
 @pytest.mark.parametrize("name", ["film", "ellipsoid", "ico8"])
@@ -56,10 +72,11 @@ def test_full_size_sampled_rows(name):
                           coupling=pkg.COUPLING_ON_THE_FLY if prec == "fp32-onfly" else pkg.COUPLING_STORED)
         y = op.matvec(x, torch.full_like(x, float("nan"))).cpu().numpy()[:, rows]
         assert pkg.h2_device_status(op.handle) == 0
-        errs[prec] = float(np.max(np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+        errs[prec] = float(np.max(rel_err(y, ref)))
+        l2 = float(np.max(np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+        print(name, prec, f"L2 {l2:.2e}, max-norm / 2 and L2 {errs[prec]:.2e}")
         del op
         torch.cuda.empty_cache()
     print(name, {k: f"{v:.2e}" for k, v in errs.items()})
-    for prec in ("fp64", "fp32", "tf32x3", "fp32-onfly"):
+    for prec in errs:
         assert errs[prec] <= TOL[prec], (prec, errs[prec])
-    assert errs["bf16x3"] <= BF16_OVER_FP32 * errs["fp32"], errs

@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle.
 
 Tolerances: the FP64 path must match the oracle's H2 product to a relative
-L2 error of 1e-8 per right-hand side, the FP32 far-field path to 1e-5; the
+error of 1e-8 per right-hand side, the reduced forms to 1e-5, in the L2
+norm, and to twice that in the max norm over the rows (see rel_err); the
 solid angles and the exact (all-near) operator agree to rounding (1e-12).
 The cluster tree and the block partition are index data and must be
 identical.
@@ -29,10 +30,22 @@ def _lib():
     pkg.load()
 
 
+# The max-norm error is held to twice the tolerance: a rounding error spread
+# over the rows peaks at a few times its root mean square, while an error
+# confined to one leaf or block at ten times the budget still fails.
+MAXNORM_FACTOR = 2.0
+
+
 def rel_err(y, ref):
+    """Per right-hand side, the larger of the relative L2 error (the metric's
+    measure) and half the relative max-norm error max_i |y_i - ref_i| / max_i
+    |ref_i|: an error confined to a few rows (one leaf, one block) dilutes in
+    the L2 norm but not in the max norm."""
     y = np.atleast_2d(y)
     ref = np.atleast_2d(ref)
-    return np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    l2 = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    mx = np.max(np.abs(y - ref), axis=1) / np.max(np.abs(ref), axis=1)
+    return np.maximum(l2, mx / MAXNORM_FACTOR)
 
 
 MESHES = {
@@ -113,13 +126,18 @@ def test_fp64_matvec_matches_oracle(name, mk, m_, leaf, r, schedule):
 
 
 PRECISIONS = {"fp32": 1, "tf32x3": 2, "bf16x3": 3}
-# Error budgets of the reduced forms against the FP64 oracle.  FP32 and 3xTF32
-# meet the 1e-5 target of the mixed forms.  BF16 hi + lo keeps about 17
-# significant bits (|a - hi - lo| <= 2^-17 |a|), 2^7 times FP32's per-entry
-# rounding; on these meshes the far-field sums amplify per-entry rounding
-# about 7-30x (FP32 measured 1e-8 .. 5e-7), so its budget is 1e-4 (1.5e-5
-# measured on the 64 x 64 cube).
-REDUCED_TOL = {"fp32": MIXED_TOL, "tf32x3": MIXED_TOL, "bf16x3": 1e-4}
+# Error budgets of the reduced forms against the FP64 oracle.  FP32 and
+# 3xTF32: the mixed-path target 1e-5.  BF16 hi + lo: the vectors enter the
+# tensor cores as three BF16 words hi + mid + lo (their FP32 values exactly)
+# and the transfers and leaf bases are FP32, so the form's one 17-bit
+# rounding is the storage of the couplings, |S - hi - lo| <= 2^-18 |S| =
+# 3.8e-6 |S| per entry; the far-field sums of these operators amplify
+# per-entry rounding 3-10 times (the FP32 form: 6e-8 per entry, 2e-7 to
+# 1.6e-6 measured), which gives the fixed budget 2e-5.  Measured 5e-6 to
+# 1.3e-5 (the latter on the 64 x 64 cube): BF16 hi + lo meets the metric's
+# 1e-5 on some workloads only, and is reported with its error.
+BF16_TOL = 2e-5
+REDUCED_TOL = {"fp32": MIXED_TOL, "tf32x3": MIXED_TOL, "bf16x3": BF16_TOL}
 
 
 @pytest.mark.parametrize("precision", sorted(PRECISIONS))
@@ -296,7 +314,7 @@ def test_split_form_runs_and_matches_oracle(precision):
         ref = o.matvec(x)
         y = op.matvec(torch.from_numpy(x).cuda(), nan_out(torch.from_numpy(x).cuda())).cpu().numpy()
         assert pkg.h2_device_status(op.handle) == 0
-        err = np.max(np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1))
+        err = np.max(rel_err(y, ref))
         assert err <= REDUCED_TOL[precision], (r, err)
 
 
@@ -345,7 +363,7 @@ def test_paired_near_field_within_budget(precision):
         y64 = op64.matvec(xt).cpu().numpy()
         assert pkg.h2_device_status(op.handle) == 0
         nrm = np.linalg.norm(ref, axis=1)
-        err = np.max(np.linalg.norm(y - ref, axis=1) / nrm)
+        err = np.max(rel_err(y, ref))
         assert err <= REDUCED_TOL[precision], (r, err)
         assert np.max(np.linalg.norm(y - y64, axis=1) / nrm) <= 1e-6, r
 
@@ -375,5 +393,5 @@ def test_autotuner_with_split_and_tile_pipe_candidates():
         for _ in range(3):   # direct launch, graph capture, graph replay
             y = op.matvec(xt, nan_out(xt)).cpu().numpy()
             assert pkg.h2_device_status(op.handle) == 0
-            err = np.max(np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1))
+            err = np.max(rel_err(y, ref))
             assert err <= REDUCED_TOL[precision], (precision, r, err)
