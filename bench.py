@@ -371,10 +371,12 @@ def roofline_of(launch, r, precision, peaks, peak_src, workload):
     fp64_peak = N_SM * FP64_FMA_PER_CLK_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
     fp32_peak = N_SM * FP32_FMA_PER_CLK_SM * 2 * sm_max * 1e6 / 1e12
     pair_peak = N_SM * FP32_FMA_PER_CLK_SM / PAIR_INSTR_PER_MAC * 2 * sm_max * 1e6 / 1e12
+    k = launch["kind"]
+    if k in (8, 9, 10):   # the split form runs products of at most 16 right-hand sides
+        r = min(r, 16)
     t = launch["ms"] / 1e3
     gbs = launch["bytes"] / t / 1e9
     tfl = 2.0 * launch["macs_per_rhs"] * r / t / 1e12
-    k = launch["kind"]
     if k == 8:   # the split form's near field: FP64 FMAs, or the paired form's FP32 instructions
         pair = precision.endswith("-pair")
         alu_peak, alu_name = (pair_peak, f"FP32 pipe at {PAIR_INSTR_PER_MAC} instructions per multiply-add "

@@ -1179,6 +1179,25 @@ struct NStage {
     int32_t seg, last, npieces, out_row, nrows;
 };
 
+// NJ (row, right-hand side) items of one thread over the columns of a staged
+// FP64 near block (column-major, nrows rows; inputs r values per column).
+// NJ is the same for every lane of a warp, so a warp whose item slots lie
+// beyond the unit's items issues no FP64 instruction for them: an FMA with
+// its lanes predicated off would still hold the FP64 pipe.
+// Item j of a thread is packed as row | (right-hand side << 8) (rows <= 64,
+// right-hand sides <= 16), so that the items fit the kernel's 40 registers.
+template <int NJ, int JM>
+__device__ __forceinline__ void near_item_cols(const double* __restrict__ A, const double* __restrict__ x, int nrows,
+                                               int r, int ncols, const int (&item)[JM], double (&acc)[JM]) {
+#pragma unroll 1
+    for (int col = 0; col < ncols; ++col) {
+        const double* Ac = A + col * nrows;
+        const double* xc = x + col * r;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) acc[j] = fma(Ac[item[j] & 0xFF], xc[item[j] >> 8], acc[j]);
+    }
+}
+
 // At most 40 registers per thread: one CTA of this kernel and one of the
 // far-field launch at r <= 16 (288 threads x 128 registers) share each SM
 // sub-partition's 16 K registers even where three warps of each meet.
@@ -1293,7 +1312,8 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
             lo[j] = 0.0f;
         }
         int cur = -1, nitems = 0, nrows = 1;
-        int irow[JM], icol[JM];   // item j of this thread: output row, right-hand side
+        int item[JM];             // item j of this thread: output row | (right-hand side << 8)
+        int nj = 0;               // item slots of this warp that hold items (the same on every lane)
         // PAIR: one output row and up to four consecutive right-hand sides per
         // thread (64 rows x 16 right-hand sides fill the 256 threads), so that
         // one entry load serves four products
@@ -1316,11 +1336,14 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
                     prhs0 = tid / nrows * 4;
                     pcnt = tid < nrows * ((r + 3) / 4) ? min(4, r - prhs0) : 0;
                 } else {
+                    // slot j of lane l of warp w: item 32 w + l + 256 j; slots past the
+                    // items point at item 0 (their sums are never written)
+                    nj = 0;
 #pragma unroll
                     for (int j = 0; j < JM; ++j) {
                         const int it = tid + kNearCons * j;
-                        irow[j] = it % nrows;
-                        icol[j] = it / nrows;
+                        item[j] = it < nitems ? (it % nrows) | ((it / nrows) << 8) : 0;
+                        if ((tid & ~31) + kNearCons * j < nitems) nj = j + 1;
                     }
                 }
             }
@@ -1353,13 +1376,13 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
                 } else {
                     const double* A = reinterpret_cast<const double*>(stg + P.smem_off);
                     const double* x = reinterpret_cast<const double*>(xin + P.xoff);
-#pragma unroll 2
-                    for (int col = 0; col < P.ncols; ++col) {
-                        const double* Ac = A + col * nrows;
-                        const double* xc = x + col * r;
-#pragma unroll
-                        for (int j = 0; j < JM; ++j)
-                            if (tid + kNearCons * j < nitems) acc[j] = fma(Ac[irow[j]], xc[icol[j]], acc[j]);
+                    static_assert(JM == 4, "the FP64 item form is instantiated for 16 right-hand sides");
+                    switch (nj) {   // warp-uniform
+                        case 4: near_item_cols<4>(A, x, nrows, r, P.ncols, item, acc); break;
+                        case 3: near_item_cols<3>(A, x, nrows, r, P.ncols, item, acc); break;
+                        case 2: near_item_cols<2>(A, x, nrows, r, P.ncols, item, acc); break;
+                        case 1: near_item_cols<1>(A, x, nrows, r, P.ncols, item, acc); break;
+                        default: break;
                     }
                 }
             }
@@ -1373,7 +1396,8 @@ __global__ void __maxnreg__(40) k_near_items(const NArgs a) {
                                       (double)hi[j] + (double)lo[j]);
                     } else {
                         if (tid + kNearCons * j < nitems)
-                            atomicAdd(a.u2n + (int64_t)icol[j] * a.N + a.perm[D.out_row + irow[j]], acc[j]);
+                            atomicAdd(a.u2n + (int64_t)(item[j] >> 8) * a.N + a.perm[D.out_row + (item[j] & 0xFF)],
+                                      acc[j]);
                     }
                     acc[j] = 0.0;
                     hi[j] = 0.0f;
