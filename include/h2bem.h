@@ -91,6 +91,9 @@ typedef struct {
     int32_t autotune;       /* 1: h2_assemble ends with h2_autotune(op, max_rhs)       */
     int32_t coupling;       /* h2_coupling: stored S_ts (default) or evaluated        */
     int32_t near_field;     /* h2_near_field: near-field arithmetic (default FP64)     */
+    double recompress_eps;  /* 0 (default): interpolation bases of rank k = m^3; in
+                               (0, 1): algebraic recompression of the far field with
+                               relative threshold eps (see h2_assemble)              */
 } h2_params;
 
 /* H2_COUPLING_STORED (default): the coupling matrices S_ts are assembled and
@@ -154,7 +157,21 @@ int h2_build_geometry(const double* xyz, int64_t n_vertices, const int32_t* tri,
 /* Assemble the H2 operator on the device (Section "H2-Matrix Compression"):
  * cluster tree, block partition, leaf bases V_t and W_t, transfer matrices
  * E_t, coupling matrices S_ts and FP64 Lindholm near blocks with the
- * solid-angle diagonal.  `p` may be NULL (defaults).  Synchronous. */
+ * solid-angle diagonal.  `p` may be NULL (defaults).  Synchronous.
+ * With p->recompress_eps = eps > 0 the far field is then compressed
+ * algebraically on the device, in FP64, before it is stored in the operator's
+ * precision (the paper's recompression of the cluster bases after their
+ * construction, Section "H2-Matrix Compression"; the steps of Boerm's
+ * algorithms for nested bases): the row and column bases are orthogonalised
+ * (QR, leaves to root), their total weights formed (root to leaves) and
+ * truncated to the left singular vectors whose singular values exceed eps
+ * times the largest (leaves to root), which gives every cluster its own rank
+ * <= k and new couplings B_t S_ts B_s^T.  The product's error against the
+ * interpolation operator is about 0.02 eps on the benchmark meshes; the
+ * streamed bytes fall with the ranks (h2_stats).  Needs stored couplings
+ * (H2_COUPLING_STORED); H2_ERR_INVALID_ARG for eps < 0 or eps >= 1.  The
+ * recompression uses FP64 scratch of about the interpolation far field's
+ * FP64 size twice over, released before the call returns. */
 int h2_assemble(const h2_handle* geom, const h2_params* p, h2_handle** out_op);
 
 /* u2 = M u1 for r right-hand sides (Eq. (denseMat)).
@@ -256,6 +273,11 @@ typedef struct {
     int64_t bytes_near_pair;       /* device bytes of the paired near-field copy (0
                                       unless h2_params.near_field = H2_NEAR_F32PAIR)   */
     int32_t near_field, coupling;  /* h2_near_field and h2_coupling of the operator     */
+    double recompress_eps;         /* h2_params.recompress_eps of the operator           */
+    double mean_rank_row;          /* mean rank of the row bases the product uses (k
+                                      without recompression)                            */
+    double mean_rank_col;          /* the same for the column bases                     */
+    int32_t max_rank;              /* the largest rank of a cluster basis               */
 } h2_stats_t;
 
 int h2_stats(const h2_handle* op, h2_stats_t* out);

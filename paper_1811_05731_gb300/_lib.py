@@ -44,7 +44,8 @@ class Params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("leaf", ctypes.c_int32), ("eta", ctypes.c_double),
                 ("box_inflation", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("max_rhs", ctypes.c_int32), ("schedule", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("coupling", ctypes.c_int32), ("near_field", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32), ("coupling", ctypes.c_int32), ("near_field", ctypes.c_int32),
+                ("recompress_eps", ctypes.c_double)]
 
 
 class PlanReport(ctypes.Structure):
@@ -79,7 +80,9 @@ class Stats(ctypes.Structure):
                 ("assemble_seconds", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("max_rhs", ctypes.c_int32), ("n_launches_matvec", ctypes.c_int32),
                 ("n_passes", ctypes.c_int32), ("bytes_near_pair", ctypes.c_int64),
-                ("near_field", ctypes.c_int32), ("coupling", ctypes.c_int32)]
+                ("near_field", ctypes.c_int32), ("coupling", ctypes.c_int32),
+                ("recompress_eps", ctypes.c_double), ("mean_rank_row", ctypes.c_double),
+                ("mean_rank_col", ctypes.c_double), ("max_rank", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -303,13 +306,13 @@ class Operator:
     def __init__(self, geom: Geometry, m: int = 4, leaf: int = 64, eta: float = 2.0,
                  rho: float = 0.25, precision: int = FP64, max_rhs: int = 1,
                  schedule: int = SCHEDULE_FLOW, autotune: bool = False,
-                 coupling: int = COUPLING_STORED, near_field: int = NEAR_FP64):
+                 coupling: int = COUPLING_STORED, near_field: int = NEAR_FP64, recompress_eps: float = 0.0):
         self.geom = geom
         self.N = geom.N
         self.params = h2_default_params(m=m, leaf=leaf, eta=eta, box_inflation=rho,
                                         precision=precision, max_rhs=max_rhs, schedule=schedule,
                                         autotune=1 if autotune else 0, coupling=coupling,
-                                        near_field=near_field)
+                                        near_field=near_field, recompress_eps=float(recompress_eps))
         self.handle = h2_assemble(geom.handle, self.params)
 
     def autotune(self, r: int | None = None, stream=None) -> dict:

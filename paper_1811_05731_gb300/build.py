@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["h2_api.cpp", "h2_host.cpp", "h2_plan.cpp", "h2_check.cpp", "h2_assemble.cu", "h2_matvec.cu"]
+SOURCES = ["h2_api.cpp", "h2_host.cpp", "h2_plan.cpp", "h2_check.cpp", "h2_assemble.cu", "h2_matvec.cu",
+           "h2_recompress.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

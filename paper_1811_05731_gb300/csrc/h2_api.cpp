@@ -52,6 +52,8 @@ void free_device(h2_handle* h) {
         if (h->near_stream) cudaStreamDestroy(h->near_stream);
         if (h->ev_fork) cudaEventDestroy(h->ev_fork);
         if (h->ev_join) cudaEventDestroy(h->ev_join);
+        delete h->rc;
+        h->rc = nullptr;
     }
 }
 
@@ -155,6 +157,9 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
     if (p.near_field == H2_NEAR_F32PAIR &&
         ((p.precision != H2_FP32 && p.precision != H2_BF16X3) || p.max_rhs <= 8))
         return H2_ERR_INVALID_ARG;
+    if (!(p.recompress_eps >= 0.0) || !(p.recompress_eps < 1.0) ||
+        (p.recompress_eps > 0.0 && p.coupling != H2_COUPLING_STORED))
+        return H2_ERR_INVALID_ARG;
     const auto t0 = std::chrono::steady_clock::now();
     h2_handle* geom = const_cast<h2_handle*>(geom_c);
     h2_handle* op = new (std::nothrow) h2_handle();
@@ -171,8 +176,15 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
     op->device = geom->device;
     h2::build_cluster_tree(op);
     h2::build_block_partition(op);
-    h2::build_plan(op);
     int rc = H2_OK;
+    if (p.recompress_eps > 0.0) {   // ranks per cluster before the product's layout
+        rc = h2::recompress_device(op, nullptr);
+        if (rc != H2_OK) {
+            release(op);
+            return rc;
+        }
+    }
+    h2::build_plan(op);
     if (p.schedule == H2_SCHEDULE_FLOW || p.autotune) {   // the autotuner may pick either schedule
         h2::FlowModel fm;
         rc = h2::flow_model(op, fm);
@@ -182,6 +194,7 @@ int h2_assemble(const h2_handle* geom_c, const h2_params* p_in, h2_handle** out_
     }
     if (rc == H2_OK) rc = h2::upload_plan(op);
     if (rc == H2_OK) rc = h2::assemble_device(op, nullptr);
+    if (op->rc) op->rc->release_device();   // the ranks stay for h2_stats
     if (rc != H2_OK) {
         release(op);
         return rc;
@@ -315,6 +328,30 @@ int h2_stats(const h2_handle* op, h2_stats_t* out) {
     out->n_near_blocks = (int64_t)op->near_t.size();
     out->near_entries = op->near_entries;
     out->far_coefficients = (int64_t)op->far_t.size() * op->k * op->k;
+    out->recompress_eps = op->params.recompress_eps;
+    out->mean_rank_row = out->mean_rank_col = op->k;
+    out->max_rank = op->k;
+    if (op->rc) {
+        out->far_coefficients = 0;
+        for (size_t b = 0; b < op->far_t.size(); ++b)
+            out->far_coefficients += (int64_t)op->rc->kr[op->far_t[b]] * op->rc->kc[op->far_s[b]];
+        double sr = 0.0, sc = 0.0;
+        int64_t nr = 0, ncn = 0;
+        out->max_rank = 0;
+        for (int c = 0; c < op->nc; ++c) {
+            if (op->need_y[c]) {
+                sr += op->rc->kr[c];
+                ++nr;
+            }
+            if (op->need_x[c]) {
+                sc += op->rc->kc[c];
+                ++ncn;
+            }
+            out->max_rank = std::max(out->max_rank, std::max(op->rc->kr[c], op->rc->kc[c]));
+        }
+        out->mean_rank_row = nr ? sr / nr : 0.0;
+        out->mean_rank_col = ncn ? sc / ncn : 0.0;
+    }
     out->basis_coefficients = op->basis_coefficients;
     out->bytes_far = op->far_bytes;
     out->bytes_near = op->near_bytes;

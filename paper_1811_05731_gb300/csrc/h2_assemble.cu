@@ -439,6 +439,28 @@ struct NearItem {
 // The paired copy of the near blocks (h2_near_field H2_NEAR_F32PAIR): every
 // FP64 value v of the near pass's arena bytes as hi = fp32(v) and
 // lo = fp32(v - hi), the exact remainder rounded once (48 significant bits).
+// One recompressed far-field matrix: an FP64 column-major source (rows x
+// cols, leading dimension ld) copied, transposed when `trans`, into an
+// arena block of `nrows` rows in the product's format `type`.
+struct StoreItem {
+    int64_t src;        // doubles into the source buffer
+    int64_t dst;        // bytes into the arena
+    int32_t ld, rows, cols, trans, nrows, type;
+};
+
+__global__ void k_store_rc(const StoreItem* __restrict__ items, const double* __restrict__ src0,
+                           const double* __restrict__ src1, unsigned char* arena) {
+    const StoreItem it = items[blockIdx.x];
+    const double* src = it.trans < 2 ? src0 : src1;   // trans bit 1: the second source buffer
+    const bool tr = (it.trans & 1) != 0;
+    const int orow = tr ? it.cols : it.rows, ocol = tr ? it.rows : it.cols;
+    for (int idx = threadIdx.x; idx < orow * ocol; idx += blockDim.x) {
+        const int i = idx % orow, j = idx / orow;
+        const double v = tr ? src[it.src + (int64_t)i * it.ld + j] : src[it.src + (int64_t)j * it.ld + i];
+        store_block(arena, it.dst, it.nrows, i, j, v, it.type);
+    }
+}
+
 __global__ void k_pair_split(const double* __restrict__ src, float2* __restrict__ dst, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double v = src[i];
@@ -503,7 +525,10 @@ int geometry_device_setup(h2_handle* g, cudaStream_t s) {
     return H2_OK;
 }
 
-int assemble_device(h2_handle* op, cudaStream_t s) {
+// Assembles the operator's matrices into `arena` at the offsets its plan
+// recorded (h2_handle::V, W, Eup, Edown, S, Nb): the interpolation far field
+// (leaf bases, transfers, couplings) when `far`, the near blocks when `near`.
+static int assemble_matrices(h2_handle* op, cudaStream_t s, unsigned char* arena, bool far, bool near) {
     const h2_handle* g = op->geom;
     const int m = op->m, k = op->k;
     // leaf bases: FP64 or FP32 column-major; coupling and transfer blocks in
@@ -514,10 +539,8 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
     const int te = transfer_piece_type(prec);    // transfers
     int rc;
 
-    H2_CUDA_TRY(cudaMalloc((void**)&op->d_arena, (size_t)std::max<int64_t>(op->arena_bytes, 16)));
-    H2_CUDA_TRY(cudaMemsetAsync(op->d_arena, 0, (size_t)std::max<int64_t>(op->arena_bytes, 16), s));
-    if ((rc = upload(op->perm, &op->d_perm, s))) return rc;
-    if ((rc = upload(op->box, &op->d_box, s))) return rc;
+    if (!op->d_perm && (rc = upload(op->perm, &op->d_perm, s))) return rc;
+    if (!op->d_box && (rc = upload(op->box, &op->d_box, s))) return rc;
 
     std::vector<void*> tmp;
     auto cleanup = [&]() {
@@ -532,7 +555,7 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
         std::memcpy(it.box, &op->box[6 * (size_t)c], sizeof(it.box));
         it.start = op->start[c];
         it.size = op->size[c];
-        if (op->V[c].off >= 0) { it.off = op->V[c].off; vi.push_back(it); }
+        if (far && op->V[c].off >= 0) { it.off = op->V[c].off; vi.push_back(it); }
     }
     std::vector<double> gx, gw;
     const int q = (3 * m) / 2;   // ceil((3m - 1) / 2)
@@ -546,7 +569,7 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
     tmp.insert(tmp.end(), {d_vi, d_gx, d_gw});
     const int kb = (k + 31) / 32 * 32;
     if (!vi.empty())
-        k_leaf_V<<<(unsigned)vi.size(), kb, 0, s>>>(d_vi, m, op->d_perm, g->d_xyz, op->d_arena, f32);
+        k_leaf_V<<<(unsigned)vi.size(), kb, 0, s>>>(d_vi, m, op->d_perm, g->d_xyz, arena, f32);
 
     // per leaf, the triangles around its nodes (column bases and near field)
     std::vector<int32_t> leaf_pos(op->nc, -1);
@@ -582,7 +605,7 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
         std::vector<WItem> wj;
         int maxw = 1;
         for (int c = 0; c < op->nc; ++c) {
-            if (op->W[c].off < 0) continue;
+            if (!far || op->W[c].off < 0) continue;
             WItem it{};
             std::memcpy(it.box, &op->box[6 * (size_t)c], sizeof(it.box));
             it.off = op->W[c].off;
@@ -599,14 +622,14 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
             const size_t smem = sizeof(double) * (size_t)maxw * k;
             H2_CUDA_TRY(cudaFuncSetAttribute(k_leaf_W, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_leaf_W<<<(unsigned)wj.size(), kb, smem, s>>>(d_wj, d_lt, m, g->d_xyz, g->d_tri, d_gx, d_gw, q,
-                                                           op->d_arena, f32);
+                                                           arena, f32);
         }
     }
 
     // transfers
     std::vector<TransferItem> ti;
     for (int c = 0; c < op->nc; ++c) {
-        if (op->Eup[c].off < 0 && op->Edown[c].off < 0) continue;
+        if (!far || (op->Eup[c].off < 0 && op->Edown[c].off < 0)) continue;
         TransferItem it{};
         std::memcpy(it.box_child, &op->box[6 * (size_t)c], sizeof(it.box_child));
         std::memcpy(it.box_parent, &op->box[6 * (size_t)op->parent[c]], sizeof(it.box_parent));
@@ -617,23 +640,23 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
     TransferItem* d_ti = nullptr;
     if ((rc = upload(ti, &d_ti, s))) { cleanup(); return rc; }
     tmp.push_back(d_ti);
-    if (!ti.empty()) k_transfer<<<(unsigned)ti.size(), kb, 0, s>>>(d_ti, m, op->d_arena, te);
+    if (!ti.empty()) k_transfer<<<(unsigned)ti.size(), kb, 0, s>>>(d_ti, m, arena, te);
 
     // coupling
-    std::vector<CouplingItem> ci(op->far_t.size());
+    std::vector<CouplingItem> ci(far ? op->far_t.size() : 0);
     for (size_t b = 0; b < ci.size(); ++b) ci[b] = {op->far_t[b], op->far_s[b], op->S[b].off};
     CouplingItem* d_ci = nullptr;
     if ((rc = upload(ci, &d_ci, s))) { cleanup(); return rc; }
     tmp.push_back(d_ci);
-    if (op->params.coupling == H2_COUPLING_ON_THE_FLY) {   // nodes only: the product evaluates S_ts
+    if (far && op->params.coupling == H2_COUPLING_ON_THE_FLY) {   // nodes only: the product evaluates S_ts
         if (!op->d_nodes) H2_CUDA_TRY(cudaMalloc((void**)&op->d_nodes, sizeof(float4) * (size_t)op->nc * op->kp));
         k_cluster_nodes<<<(unsigned)op->nc, 128, 0, s>>>(m, op->kp, op->d_box, op->d_nodes);
-        if (!ci.empty()) k_coupling_nodes<<<(unsigned)ci.size(), 128, 0, s>>>(d_ci, m, op->d_box, op->d_arena);
+        if (!ci.empty()) k_coupling_nodes<<<(unsigned)ci.size(), 128, 0, s>>>(d_ci, m, op->d_box, arena);
     } else if (!ci.empty()) {
-        k_coupling<<<(unsigned)ci.size(), 256, 0, s>>>(d_ci, m, op->d_box, op->d_arena, tt);
+        k_coupling<<<(unsigned)ci.size(), 256, 0, s>>>(d_ci, m, op->d_box, arena, tt);
     }
 
-    std::vector<NearItem> ni(op->near_t.size());
+    std::vector<NearItem> ni(near ? op->near_t.size() : 0);
     int maxleaf = 1;
     for (size_t b = 0; b < ni.size(); ++b) {
         const int t = op->near_t[b], sc = op->near_s[b];
@@ -657,12 +680,12 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
         H2_CUDA_TRY(cudaFuncSetAttribute(k_near, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int nb = (maxleaf + 31) / 32 * 32;
         k_near<<<(unsigned)ni.size(), nb, smem, s>>>(d_ni, d_lt, op->d_perm, g->d_xyz, g->d_tri,
-                                                     g->d_psi, op->d_arena);
+                                                     g->d_psi, arena);
     }
-    if (op->d_near_pair && op->near_hi > op->near_lo) {
+    if (near && op->d_near_pair && op->near_hi > op->near_lo) {
         const int64_t n = (op->near_hi - op->near_lo) / 8;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16 * 152));
-        k_pair_split<<<grid, 256, 0, s>>>(reinterpret_cast<const double*>(op->d_arena + op->near_lo),
+        k_pair_split<<<grid, 256, 0, s>>>(reinterpret_cast<const double*>(arena + op->near_lo),
                                           op->d_near_pair, n);
     }
     cudaError_t e = cudaGetLastError();
@@ -673,6 +696,58 @@ int assemble_device(h2_handle* op, cudaStream_t s) {
         return H2_ERR_CUDA;
     }
     return H2_OK;
+}
+
+// The operator's arena: the far field from the recompression when the
+// operator was recompressed (h2_params.recompress_eps > 0), else from the
+// interpolation kernels; the near blocks always.
+int assemble_device(h2_handle* op, cudaStream_t s) {
+    H2_CUDA_TRY(cudaMalloc((void**)&op->d_arena, (size_t)std::max<int64_t>(op->arena_bytes, 16)));
+    H2_CUDA_TRY(cudaMemsetAsync(op->d_arena, 0, (size_t)std::max<int64_t>(op->arena_bytes, 16), s));
+    if (op->rc) {
+        const RcResult& R = *op->rc;
+        const int prec = op->params.precision;
+        const int P = prec == H2_FP64 ? PIECE_F64 : PIECE_F32;
+        const int PT = transfer_piece_type(prec), PC = coupling_piece_type(prec);
+        std::vector<StoreItem> items;
+        auto add = [&](const RcSource& src, const MatRef& dst, int trans, int type, bool second) {
+            if (dst.off < 0 || src.rows <= 0 || src.cols <= 0) return;
+            items.push_back(StoreItem{src.off, dst.off, src.ld, src.rows, src.cols, trans | (second ? 2 : 0),
+                                      dst.nrows, type});
+        };
+        for (int c = 0; c < op->nc; ++c) {
+            // W block: kc x |c| with entry (mu, j) = Wn(j, mu); V block: |c| x kr = Vn
+            if (op->child0[c] < 0) {
+                add(R.Wn[c], op->W[c], 1, P, false);
+                add(R.Vn[c], op->V[c], 0, P, false);
+            }
+            // upward transfer into the parent: kc_p x kc_c = Fn_c^T; downward: kr_c x kr_p = En_c
+            if (op->parent[c] >= 0) {
+                add(R.Fn[c], op->Eup[c], 1, PT, false);
+                add(R.En[c], op->Edown[c], 0, PT, false);
+            }
+        }
+        for (size_t b = 0; b < op->far_t.size(); ++b) add(R.Sn[b], op->S[b], 0, PC, true);
+        StoreItem* d_items = nullptr;
+        int rc = upload(items, &d_items, s);
+        if (rc) return rc;
+        if (!items.empty()) k_store_rc<<<(unsigned)items.size(), 256, 0, s>>>(d_items, R.d_pool, R.d_interp, op->d_arena);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(d_items);
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "k_store_rc", __FILE__, __LINE__);
+            return H2_ERR_CUDA;
+        }
+        return assemble_matrices(op, s, op->d_arena, false, true);
+    }
+    return assemble_matrices(op, s, op->d_arena, true, true);
+}
+
+// The interpolation far field alone, in FP64, into `arena` at the offsets
+// the caller recorded in the operator's matrix references (recompression input).
+int assemble_interp_far(h2_handle* op, cudaStream_t s, unsigned char* arena) {
+    return assemble_matrices(op, s, arena, true, false);
 }
 
 }  // namespace h2

@@ -191,6 +191,33 @@ struct MatRef {
     int32_t nrows = 0, ncols = 0, type = 0;
 };
 
+// An FP64 column-major matrix (rows x cols, leading dimension ld) in a
+// device buffer, `off` in doubles.
+struct RcSource {
+    int64_t off = 0;
+    int32_t ld = 0, rows = 0, cols = 0;
+};
+
+// The far field of an operator after algebraic recompression
+// (h2_params.recompress_eps > 0): the ranks of every cluster's row and
+// column bases and, per matrix of the product, where its FP64 values lie
+// (d_pool: leaf bases and transfers; d_interp: the couplings, written over
+// the interpolation arena they were computed from).  Released after the
+// product's arena is assembled.
+struct RcResult {
+    double* d_pool = nullptr;
+    double* d_interp = nullptr;
+    std::vector<int32_t> kr, kc;               // per cluster (0: basis unused)
+    std::vector<RcSource> Vn, Wn, En, Fn;      // per cluster: leaf bases, transfers (rows, columns)
+    std::vector<RcSource> Sn;                  // per far block
+    void release_device() {
+        if (d_pool) cudaFree(d_pool);
+        if (d_interp) cudaFree(d_interp);
+        d_pool = d_interp = nullptr;
+    }
+    ~RcResult() { release_device(); }
+};
+
 }  // namespace h2
 
 struct h2_handle {
@@ -225,6 +252,7 @@ struct h2_handle {
     std::vector<h2::MatRef> W, V, Eup, Edown;     // per cluster
     std::vector<h2::MatRef> S;                    // per far block
     std::vector<h2::MatRef> Nb;                   // per near block
+    h2::RcResult* rc = nullptr;                   // recompressed far field until the arena holds it
     int64_t arena_bytes = 0;
     unsigned char* d_arena = nullptr;
     int32_t* d_perm = nullptr;
@@ -346,6 +374,11 @@ int build_split(h2_handle* op);             // its ticket order (host)
 // device-side assembly and matvec (h2_assemble.cu, h2_matvec.cu)
 int geometry_device_setup(h2_handle* g, cudaStream_t s);
 int assemble_device(h2_handle* op, cudaStream_t s);
+int assemble_interp_far(h2_handle* op, cudaStream_t s, unsigned char* arena);
+// Algebraic recompression of the far field on the device (h2_recompress.cu):
+// fills op->rc (ranks and FP64 matrices); build_plan then lays out the
+// product with those ranks and assemble_device stores them.
+int recompress_device(h2_handle* op, cudaStream_t s);
 int upload_plan(h2_handle* op);
 int matvec_device(h2_handle* op, const double* u1, double* u2, int r, cudaStream_t s);
 void release_graph(h2_handle* op);

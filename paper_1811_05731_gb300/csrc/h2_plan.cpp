@@ -197,6 +197,11 @@ void build_plan(h2_handle* op) {
     op->ws_rows = op->row_yhat + (int64_t)nc * kp + 4;
     auto xrow = [&](int c) { return (int32_t)(op->row_xhat + (int64_t)c * kp); };
     auto yrow = [&](int c) { return (int32_t)(op->row_yhat + (int64_t)c * kp); };
+    // ranks of the cluster bases: k everywhere for the interpolation operator,
+    // the recompression's ranks otherwise (rows of y-hat_c and of x-hat_c; the
+    // workspace slots keep their kp rows)
+    auto krow = [&](int c) { return op->rc ? op->rc->kr[c] : k; };
+    auto kcol = [&](int c) { return op->rc ? op->rc->kc[c] : k; };
 
     op->zero_rows.clear();   // workspace regions accumulated atomically, cleared by the gather
     op->W.assign(nc, MatRef{});
@@ -213,12 +218,13 @@ void build_plan(h2_handle* op) {
         std::vector<SegSpec> segs;
         for (int c = 0; c < nc; ++c) {
             if (op->child0[c] >= 0 || !op->need_x[c]) continue;
+            if (kcol(c) <= 0) continue;
             SegSpec s;
             s.out_row = xrow(c);
-            s.nrows = k;
+            s.nrows = kcol(c);
             s.mode = SEG_STORE;
             s.mats.push_back({&op->W[c], op->size[c], P, op->leaf_row[c]});
-            s.bytes = (int64_t)k * op->size[c];
+            s.bytes = (int64_t)kcol(c) * op->size[c];
             segs.push_back(s);
         }
         emit_pass(op, "up_leaf", PASS_UP_LEAF, segs, arena);
@@ -230,12 +236,13 @@ void build_plan(h2_handle* op) {
             if (op->level[c] != l || op->child0[c] < 0 || !op->need_x[c]) continue;
             op->zero_rows.push_back(xrow(c));
             for (int ch : {op->child0[c], op->child1[c]}) {
+                if (kcol(c) <= 0 || kcol(ch) <= 0) continue;
                 SegSpec s;
                 s.out_row = xrow(c);
-                s.nrows = k;
+                s.nrows = kcol(c);
                 s.mode = SEG_ATOMIC;
-                s.mats.push_back({&op->Eup[ch], k, PT, xrow(ch)});
-                s.bytes = (int64_t)k * k;
+                s.mats.push_back({&op->Eup[ch], kcol(ch), PT, xrow(ch)});
+                s.bytes = (int64_t)kcol(c) * kcol(ch);
                 segs.push_back(s);
             }
         }
@@ -263,14 +270,15 @@ void build_plan(h2_handle* op) {
             for (size_t g0 = 0; g0 < by_t[t].size(); g0 += split) {
                 SegSpec s;
                 s.out_row = yrow(t);
-                s.nrows = k;
+                s.nrows = krow(t);
                 s.mode = SEG_ATOMIC;
                 for (size_t g = g0; g < std::min(by_t[t].size(), g0 + split); ++g) {
                     const int32_t b = by_t[t][g];
-                    s.mats.push_back({&op->S[b], k, PS, xrow(op->far_s[b])});
-                    s.bytes += (int64_t)k * k;
+                    if (kcol(op->far_s[b]) <= 0) continue;
+                    s.mats.push_back({&op->S[b], kcol(op->far_s[b]), PS, xrow(op->far_s[b])});
+                    s.bytes += (int64_t)krow(t) * kcol(op->far_s[b]);
                 }
-                segs.push_back(s);
+                if (s.nrows > 0 && !s.mats.empty()) segs.push_back(s);
             }
         }
         (void)nfar;
@@ -283,12 +291,13 @@ void build_plan(h2_handle* op) {
             if (op->level[c] != l) continue;
             const int p = op->parent[c];
             if (p < 0 || !op->need_y[p]) continue;
+            if (krow(c) <= 0 || krow(p) <= 0) continue;
             SegSpec s;
             s.out_row = yrow(c);
-            s.nrows = k;
+            s.nrows = krow(c);
             s.mode = op->is_tgt[c] ? SEG_ADD : SEG_STORE;
-            s.mats.push_back({&op->Edown[c], k, PT, yrow(p)});
-            s.bytes = (int64_t)k * k;
+            s.mats.push_back({&op->Edown[c], krow(p), PT, yrow(p)});
+            s.bytes = (int64_t)krow(c) * krow(p);
             segs.push_back(s);
         }
         emit_pass(op, "down_transfer", PASS_DOWN_TRANSFER, segs, arena);
@@ -318,12 +327,13 @@ void build_plan(h2_handle* op) {
         std::vector<SegSpec> segs;
         for (int t = 0; t < nc; ++t) {
             if (op->child0[t] >= 0 || !op->need_y[t]) continue;
+            if (krow(t) <= 0) continue;
             SegSpec s;
             s.out_row = op->start[t];
             s.nrows = op->size[t];
             s.mode = SEG_FINAL_ADD;
-            s.mats.push_back({&op->V[t], k, P, yrow(t)});
-            s.bytes = (int64_t)op->size[t] * k * (P == PIECE_F64 ? 2 : 1);
+            s.mats.push_back({&op->V[t], krow(t), P, yrow(t)});
+            s.bytes = (int64_t)op->size[t] * krow(t) * (P == PIECE_F64 ? 2 : 1);
             segs.push_back(s);
         }
         emit_pass(op, "leaf_expand", PASS_LEAF_EXPAND, segs, arena);
