@@ -368,8 +368,52 @@ typedef struct {
 int h2_plan_check(const double* xyz, int64_t n_vertices, const int32_t* tri, int64_t n_triangles,
                   const h2_params* params, int32_t workers, h2_plan_report_t* out);
 
-/* Release a geometry or operator handle; NULL is a no-op.  Releasing a handle
- * twice is undefined. */
+/* ---- The finite-element half of the field evaluation ----
+ * Section "Basic Equations" (Fredkin-Koehler): the magnetostatic potential
+ * u = u1 + u2 of a body with magnetisation M, on a tetrahedral mesh with
+ * linear (P1) elements:
+ *   u1: Poisson problem with Neumann data M.n (Eqs. u1Poiss, u1Neumann),
+ *       weak form int grad u1 . grad v = int M . grad v for all P1 v, made
+ *       unique by a zero mean (lumped volume weights);
+ *   u2: harmonic, boundary values from the boundary integral equation
+ *       (Eq. mainInt) = the operator's product with u1 on the boundary
+ *       (h2_matvec), interior values from the P1 Dirichlet problem;
+ *   e_d / K_d = (1/V) int M . grad(u1 + u2) dV, K_d = mu0 Ms^2 / 2 (Section
+ *       "Magnetostatic field and energy"; for a uniform unit M the
+ *       demagnetising factor along M).
+ * Both linear systems are solved on the device by conjugate gradients
+ * preconditioned with the stiffness matrix's diagonal (FP64). */
+
+/* Build a tetrahedral-mesh handle (host arrays, copied):
+ *   xyz:  n_vertices x 3 doubles;  tets: n_tets x 4 int32 vertex indices,
+ *         each tetrahedron of positive volume (H2_ERR_MESH_ORIENTATION
+ *         otherwise);
+ *   surf_nodes: the volume index of every node of the boundary surface, in
+ *         the node order of the surface mesh the operator was built on
+ *         (h2_build_geometry of the boundary faces, outward).
+ * Assembles the P1 stiffness matrix (CSR) and the element volumes and
+ * gradients on the current device.  Synchronous. */
+int h2_fem_create(const double* xyz, int64_t n_vertices, const int32_t* tets, int64_t n_tets,
+                  const int32_t* surf_nodes, int64_t n_surf, h2_handle** out_fem);
+
+typedef struct {
+    int32_t iters_u1, iters_u2;   /* conjugate-gradient iterations of the two solves       */
+    double resid_u1, resid_u2;    /* their final relative residuals |r| / |b|              */
+    double energy;                /* e_d / K_d                                             */
+    double volume;                /* the body's volume (sum of the tetrahedra)             */
+} h2_fem_report_t;
+
+/* u1, u2 and the energy for the magnetisation M (DEVICE, n_tets x 3 doubles,
+ * one vector per tetrahedron).  u1, u2: DEVICE, n_vertices doubles each,
+ * overwritten.  `op`: an operator on the boundary surface (its N = n_surf).
+ * The solves stop at |r| <= tol |b| or after max_iter iterations each (see
+ * the report).  Allocates scratch for the call; synchronous on
+ * `cuda_stream`. */
+int h2_fem_solve(h2_handle* fem, h2_handle* op, const double* M, double* u1, double* u2, double tol,
+                 int32_t max_iter, void* cuda_stream, h2_fem_report_t* out);
+
+/* Release a geometry, operator or tetrahedral-mesh handle; NULL is a no-op.
+ * Releasing a handle twice is undefined. */
 int h2_free(h2_handle* h);
 
 /* Static string naming a status code. */

@@ -11,8 +11,11 @@ package only marshals arguments to it.  The functions carry the C names:
   (Section "H2-Matrix Compression")
 * :func:`h2_matvec`         - u2 = M u1 for r right-hand sides (Eq. denseMat)
 * :func:`h2_free`           - release a handle
+* :func:`h2_fem_create`, :func:`h2_fem_solve` - the finite-element half of the
+  field evaluation on a tetrahedral mesh (u1 Neumann solve, u2 boundary values
+  through the operator and Dirichlet solve, energy; Section "Basic Equations")
 
-:class:`Geometry` and :class:`Operator` wrap the handles.  There is no CPU
+:class:`Geometry`, :class:`Operator` and :class:`Fem` wrap the handles.  There is no CPU
 fallback: if the library is missing or cannot be loaded, every call raises.
 """
 from ._lib import (  # noqa: F401
@@ -21,6 +24,6 @@ from ._lib import (  # noqa: F401
     h2_default_params, h2_build_geometry, h2_assemble, h2_matvec, h2_matvec_noalloc, h2_free,
     h2_stats, h2_plan_check, PlanReport,
     h2_get_tree, h2_get_blocks, h2_get_psi, h2_device_status, h2_error_string,
-    Geometry, Operator,
+    Geometry, Operator, Fem, FemReport, h2_fem_create, h2_fem_solve,
 )
 from .build import build, lib_path  # noqa: F401

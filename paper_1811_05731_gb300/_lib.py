@@ -121,10 +121,14 @@ def load(path: str | None = None):
         L.h2_free.argtypes = [_vp]
         L.h2_plan_check.argtypes = [_c_d, ctypes.c_int64, _c_i32, ctypes.c_int64, ctypes.POINTER(Params),
                                     ctypes.c_int32, ctypes.POINTER(PlanReport)]
+        L.h2_fem_create.argtypes = [_c_d, ctypes.c_int64, _c_i32, ctypes.c_int64, _c_i32, ctypes.c_int64,
+                                    ctypes.POINTER(_vp)]
+        L.h2_fem_solve.argtypes = [_vp] * 5 + [ctypes.c_double, ctypes.c_int32, _vp, ctypes.c_void_p]
         for f in ("h2_build_geometry", "h2_assemble", "h2_matvec", "h2_matvec_noalloc", "h2_matvec_batched",
                   "h2_autotune", "h2_fault_inject_stall",
                   "h2_stats", "h2_get_tree",
-                  "h2_get_blocks", "h2_get_psi", "h2_device_status", "h2_free", "h2_plan_check"):
+                  "h2_get_blocks", "h2_get_psi", "h2_device_status", "h2_free", "h2_plan_check",
+                  "h2_fem_create", "h2_fem_solve"):
             getattr(L, f).restype = ctypes.c_int
         _LIB = L
         return L
@@ -348,6 +352,65 @@ class Operator:
         y = torch.empty_like(x) if u2 is None else u2.view(x.shape)
         h2_matvec(self.handle, x.data_ptr(), y.data_ptr(), x.shape[0], stream)
         return y if u1.dim() == 2 else y.view(-1)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            h2_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FemReport(ctypes.Structure):
+    _fields_ = [("iters_u1", ctypes.c_int32), ("iters_u2", ctypes.c_int32), ("resid_u1", ctypes.c_double),
+                ("resid_u2", ctypes.c_double), ("energy", ctypes.c_double), ("volume", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def h2_fem_create(xyz, tets, surf_nodes) -> int:
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    surf = np.ascontiguousarray(surf_nodes, dtype=np.int32)
+    h = _vp()
+    _check(lib().h2_fem_create(xyz.ctypes.data_as(_c_d), xyz.shape[0], tets.ctypes.data_as(_c_i32), tets.shape[0],
+                               surf.ctypes.data_as(_c_i32), surf.shape[0], ctypes.byref(h)), "h2_fem_create")
+    return h.value
+
+
+def h2_fem_solve(fem: int, op: int, M_ptr: int, u1_ptr: int, u2_ptr: int, tol: float, max_iter: int,
+                 stream=None) -> dict:
+    rep = FemReport()
+    _check(lib().h2_fem_solve(fem, op, M_ptr, u1_ptr, u2_ptr, float(tol), int(max_iter), _stream_ptr(stream),
+                              ctypes.byref(rep)), "h2_fem_solve")
+    return rep.as_dict()
+
+
+class Fem:
+    """Tetrahedral mesh of the magnetic body (P1 elements) on the GPU, with its
+    boundary surface given as the volume index of every surface node."""
+
+    def __init__(self, xyz, tets, surf_nodes):
+        self.nv = int(np.asarray(xyz).shape[0])
+        self.nt = int(np.asarray(tets).shape[0])
+        self.handle = h2_fem_create(xyz, tets, surf_nodes)
+
+    def solve(self, op: "Operator", M, tol: float = 1e-12, max_iter: int = 5000, stream=None):
+        """(u1, u2, report) for the magnetisation M: a (3,) vector (uniform) or
+        an (n_tets, 3) array, numpy or a torch CUDA tensor."""
+        import torch
+        Mt = torch.as_tensor(np.broadcast_to(np.asarray(M, dtype=np.float64), (self.nt, 3)).copy()
+                             if not isinstance(M, torch.Tensor) else M, dtype=torch.float64).cuda().contiguous()
+        u1 = torch.empty(self.nv, dtype=torch.float64, device="cuda")
+        u2 = torch.empty_like(u1)
+        rep = h2_fem_solve(self.handle, op.handle, Mt.data_ptr(), u1.data_ptr(), u2.data_ptr(), tol, max_iter,
+                           stream)
+        return u1, u2, rep
 
     def close(self):
         if getattr(self, "handle", None):

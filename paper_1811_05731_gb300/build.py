@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["h2_api.cpp", "h2_host.cpp", "h2_plan.cpp", "h2_check.cpp", "h2_assemble.cu", "h2_matvec.cu",
-           "h2_recompress.cu"]
+           "h2_recompress.cu", "h2_fem.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

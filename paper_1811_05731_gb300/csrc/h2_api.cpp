@@ -38,6 +38,9 @@ void free_device(h2_handle* h) {
     };
     if (h->kind == 1) {
         f(h->d_xyz); f(h->d_tri); f(h->d_adj_ptr); f(h->d_adj); f(h->d_psi);
+    } else if (h->kind == 3) {
+        h2::fem_release(h->fem);
+        h->fem = nullptr;
     } else {
         h2::release_graph(h);
         if (h->capture_stream) cudaStreamDestroy(h->capture_stream);

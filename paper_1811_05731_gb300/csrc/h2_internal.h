@@ -36,6 +36,9 @@ inline int chunk_cols_for(int max_rhs) { return max_rhs > 8 ? 64 : H2_MAX_CHUNK_
 
 namespace h2 {
 
+struct FemData;   // a tetrahedral mesh on the device (h2_fem.cu)
+void fem_release(FemData* f);
+
 enum SegMode : int32_t {
     SEG_STORE = 0,      // ws[out_row + i] = sum
     SEG_ATOMIC = 1,     // atomicAdd(ws[out_row + i], sum)
@@ -221,7 +224,8 @@ struct RcResult {
 }  // namespace h2
 
 struct h2_handle {
-    int kind = 0;   // 1 geometry, 2 operator
+    int kind = 0;   // 1 geometry, 2 operator, 3 tetrahedral mesh (FEM)
+    h2::FemData* fem = nullptr;
     int refcount = 1;
     uint64_t serial = 0;   // unique per handle (keys the batched-launch plans)
 

@@ -67,9 +67,14 @@ def test_full_size_sampled_rows(name):
     g = pkg.Geometry(w.mesh.xyz, w.mesh.tri)
     x = torch.from_numpy(np.ascontiguousarray(w.u1)).cuda()
     errs = {}
-    for prec in ("fp64", "fp32", "tf32x3", "bf16x3", "fp32-onfly"):
-        op = pkg.Operator(g, m=w.m, leaf=w.leaf, eta=w.eta, precision=PREC[prec], max_rhs=w.r,
-                          coupling=pkg.COUPLING_ON_THE_FLY if prec == "fp32-onfly" else pkg.COUPLING_STORED)
+    # the film also recompressed (eps = 1e-6) in FP64 and FP32: the product stays
+    # within the recompression's error (about 0.02 eps) of the interpolation operator
+    forms = ["fp64", "fp32", "tf32x3", "bf16x3", "fp32-onfly"] + (["fp64@1e-6", "fp32@1e-6"] if name == "film" else [])
+    for prec in forms:
+        base, eps = (prec.split("@")[0], float(prec.split("@")[1])) if "@" in prec else (prec, 0.0)
+        op = pkg.Operator(g, m=w.m, leaf=w.leaf, eta=w.eta, precision=PREC[base], max_rhs=w.r,
+                          coupling=pkg.COUPLING_ON_THE_FLY if prec == "fp32-onfly" else pkg.COUPLING_STORED,
+                          recompress_eps=eps)
         y = op.matvec(x, torch.full_like(x, float("nan"))).cpu().numpy()[:, rows]
         assert pkg.h2_device_status(op.handle) == 0
         errs[prec] = float(np.max(rel_err(y, ref)))
@@ -79,4 +84,6 @@ def test_full_size_sampled_rows(name):
         torch.cuda.empty_cache()
     print(name, {k: f"{v:.2e}" for k, v in errs.items()})
     for prec in errs:
-        assert errs[prec] <= TOL[prec], (prec, errs[prec])
+        base = prec.split("@")[0]
+        tol = TOL[base] if "@" not in prec else max(TOL[base], 0.1 * float(prec.split("@")[1]))
+        assert errs[prec] <= tol, (prec, errs[prec])
