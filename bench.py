@@ -482,6 +482,42 @@ def bench_form(pkg, torch, name, meshes, geoms, m, leaf, eta, us, precision, ste
     return out
 
 
+def bench_fem(pkg, torch, n, steps, peaks):
+    """The finite-element half of the field evaluation (h2_fem_solve) on the
+    unit ball (the [-1, 1]^3 grid of n^3 cells, six tetrahedra each, mapped
+    radially), uniform magnetisation along z: u1 Neumann solve, u2 boundary
+    values through the H2 product (m = 4, leaf 64, FP64), u2 Dirichlet solve,
+    energy.  One step = one field evaluation; CG to |r| <= 1e-10 |b|."""
+    from synth import volume as vm
+    xyz, tets = vm.ball_tets(n)
+    surf, nodes = vm.boundary_surface(xyz, tets)
+    g = pkg.Geometry(surf.xyz, surf.tri)
+    op = pkg.Operator(g, m=4, leaf=64)
+    F = pkg.Fem(xyz, tets, nodes)
+    M = torch.tensor([[0.0, 0.0, 1.0]], dtype=torch.float64).repeat(len(tets), 1).cuda()
+    F.solve(op, M, tol=1e-10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        _, _, rep = F.solve(op, M, tol=1e-10)
+    t = (time.perf_counter() - t0) / steps
+    # CSR entries: each tetrahedron edge couples two nodes (both directions) plus the diagonal
+    edges = np.unique(np.sort(np.concatenate([tets[:, [a, b]] for a in range(4) for b in range(a + 1, 4)]), axis=1),
+                      axis=0)
+    nnz = 2 * len(edges) + len(xyz)
+    iters = rep["iters_u1"] + rep["iters_u2"]
+    # per CG iteration: the CSR values and column indices once, ~10 vector passes of 8 bytes
+    cg_bytes = iters * (12 * nnz + 4 * len(xyz) + 80 * len(xyz))
+    hbm = float(peaks.get("hbm_gbs", HBM_GBS_FALLBACK))
+    return {"workload": f"fem_ball{n}", "vertices": int(len(xyz)), "tetrahedra": int(len(tets)),
+            "surface_nodes": int(len(nodes)), "ms_per_step": t * 1e3,
+            "cg_iterations": [rep["iters_u1"], rep["iters_u2"]],
+            "resid": [rep["resid_u1"], rep["resid_u2"]], "energy": rep["energy"],
+            "err_vs_one_third": abs(rep["energy"] - 1.0 / 3.0), "volume_dof_per_s": len(xyz) / t,
+            "timing": "host wall clock around the synchronous call (two CG solves with residual reads, one H2 product)",
+            "cg_gbs_lower_bound": cg_bytes / t / 1e9, "cg_hbm_frac_lower_bound": cg_bytes / t / 1e9 / hbm}
+
+
 def run_gpu(args, rank, local, world):
     import torch
     import paper_1811_05731_gb300 as pkg
@@ -608,6 +644,10 @@ def run_gpu(args, rank, local, world):
                 wr, _, wn, wel = exact_rows_rate(wmeshes[0], wus[0], 2.0)
                 cpu_by[f"{wname}/r{rr}"] = {"value": wr, "rows": wn, "seconds": wel}
 
+    fem_rec = None
+    if not args.no_forms and world == 1:
+        fem_rec = bench_fem(pkg, torch, 48, 5, peaks)
+
     cfg = {"workload": name, "N": N, "triangles": int(sum(mm.n_triangles for mm in meshes)), "m": m,
            "leaf": leaf, "eta": eta, "r": r, "precision": args.precision, "schedule": "flow",
            "note": note, "parallelism": f"replicas x{world}",
@@ -631,6 +671,7 @@ def run_gpu(args, rank, local, world):
         "cpu_baseline": cpu,
         "cpu_oracle_by_workload": cpu_by,
         "forms": forms,
+        "fem": fem_rec,
         "h2": {k: st[k] for k in ("n_clusters", "n_levels", "n_far_blocks", "n_near_blocks",
                                   "near_entries", "bytes_streamed", "macs_per_rhs",
                                   "compression_ratio", "assemble_seconds")},

@@ -187,16 +187,23 @@ __global__ void k_cg_init(int64_t n, const int32_t* __restrict__ rowptr, const i
     block_add(bb, S + 3);
 }
 
-// q = mask A p; pq_it = p . q.
+// The iteration kernels read the iteration number it from cnt[0] (so that
+// a captured sequence of iterations can be replayed): k_cg_dir's last CTA
+// advances it.  They loop over their rows with a grid stride, so that a grid
+// of a few hundred CTAs makes each reduction a few hundred atomic additions.
+
+// q = mask A p; pq_it = p . q (one thread per row: measured faster than
+// several lanes per row, whose rows of about 15 entries leave lanes idle).
 __global__ void k_cg_q(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                        const double* __restrict__ val, const unsigned char* __restrict__ mask,
-                       const double* __restrict__ p, double* __restrict__ q, double* __restrict__ S, int it) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                       const double* __restrict__ p, double* __restrict__ q, double* __restrict__ S,
+                       const int32_t* __restrict__ cnt) {
+    const int it = cnt[0];
     double pq = 0.0;
-    if (i < n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double qi = (!mask || mask[i]) ? row_dot(rowptr, col, val, p, i) : 0.0;
         q[i] = qi;
-        pq = p[i] * qi;
+        pq += p[i] * qi;
     }
     block_add(pq, S + 4 * (int64_t)it + 1);
 }
@@ -205,33 +212,43 @@ __global__ void k_cg_q(int64_t n, const int32_t* __restrict__ rowptr, const int3
 __global__ void k_cg_update(int64_t n, const unsigned char* __restrict__ mask, const double* __restrict__ diag,
                             double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
                             const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ S,
-                            int it) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                            const int32_t* __restrict__ cnt) {
+    const int it = cnt[0];
     const double pq = S[4 * (int64_t)it + 1];
     const double alpha = pq != 0.0 ? S[4 * (int64_t)it] / pq : 0.0;
     double rz = 0.0, rr = 0.0;
-    if (i < n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         x[i] += alpha * p[i];
         const double ri = r[i] - alpha * q[i];
         const double zi = (!mask || mask[i]) ? ri / diag[i] : 0.0;
         r[i] = ri;
         z[i] = zi;
-        rz = ri * zi;
-        rr = ri * ri;
+        rz += ri * zi;
+        rr += ri * ri;
     }
     block_add(rz, S + 4 * (int64_t)(it + 1));
     __syncthreads();
     block_add(rr, S + 4 * (int64_t)(it + 1) + 2);
 }
 
-// beta = rz_{it+1} / rz_it; p = z + beta p.
+// beta = rz_{it+1} / rz_it; p = z + beta p; the last CTA to finish advances
+// the iteration number (every CTA has read it by then).
 __global__ void k_cg_dir(int64_t n, double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ S,
-                         int it) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+                         int32_t* __restrict__ cnt) {
+    const int it = cnt[0];
     const double rz0 = S[4 * (int64_t)it];
     const double beta = rz0 != 0.0 ? S[4 * (int64_t)(it + 1)] / rz0 : 0.0;
-    p[i] = z[i] + beta * p[i];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = z[i] + beta * p[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(cnt + 1, 1) == (int)gridDim.x - 1) {
+            cnt[1] = 0;
+            cnt[0] = it + 1;
+            __threadfence();
+        }
+    }
 }
 
 // *acc += sum_i w_i x_i (w NULL: all ones)
@@ -302,40 +319,76 @@ int fem_upload(const std::vector<T>& v, T** d) {
     return H2_OK;
 }
 inline unsigned grid_of(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + kFemThreads - 1) / kFemThreads); }
+// CTAs of the iteration kernels (grid-stride loops): two per SM; measured
+// faster than a CTA per 256 rows (more same-address atomic additions per
+// reduction) on balls of 36k-275k nodes
+constexpr unsigned kCgCtas = 304;
+inline unsigned cg_grid(int64_t rows) { return std::min<unsigned>(grid_of(rows), kCgCtas); }
 
 // Preconditioned conjugate gradients for A x = b on the rows with mask 1
 // (mask NULL: all), x starting from its content; stops when |r| <= tol |b|
-// (checked every kCgCheck iterations) or after max_iter iterations.
+// (checked every kCgCheck iterations) or after max_iter iterations.  The
+// iterations run as a CUDA graph of kCgCheck of them (captured on a stream of
+// its own, replayed on s): the host reads one residual per replay.
 int fem_cg(const FemData& F, const unsigned char* mask, const double* b, double* x, double* work, double tol,
            int max_iter, cudaStream_t s, int* iters, double* resid) {
     const int64_t n = F.nv;
     double *r = work, *z = work + n, *p = work + 2 * n, *q = work + 3 * n;
     double* S = nullptr;
+    int32_t* cnt = nullptr;
     const size_t nscal = 4 * ((size_t)max_iter + 2);
     H2_CUDA_TRY(cudaMalloc((void**)&S, sizeof(double) * nscal));
-    H2_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(double) * nscal, s));
-    const unsigned g = grid_of(n);
-    k_cg_init<<<g, kFemThreads, 0, s>>>(n, F.rowptr, F.col, F.val, mask, b, x, r, z, p, F.diag, S);
-    double h0[4];
-    cudaError_t e = cudaMemcpyAsync(h0, S, sizeof(h0), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaMalloc((void**)&cnt, sizeof(int32_t) * 2);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S, 0, sizeof(double) * nscal, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * 2, s);
+    const unsigned gv = cg_grid(n);
+    auto iteration = [&](cudaStream_t t) {
+        k_cg_q<<<gv, kFemThreads, 0, t>>>(n, F.rowptr, F.col, F.val, mask, p, q, S, cnt);
+        k_cg_update<<<gv, kFemThreads, 0, t>>>(n, mask, F.diag, x, r, z, p, q, S, cnt);
+        k_cg_dir<<<gv, kFemThreads, 0, t>>>(n, p, z, S, cnt);
+    };
+    if (e == cudaSuccess) {
+        k_cg_init<<<grid_of(n), kFemThreads, 0, s>>>(n, F.rowptr, F.col, F.val, mask, b, x, r, z, p, F.diag, S);
+        e = cudaGetLastError();
+    }
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && max_iter >= kCgCheck) {
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int k = 0; k < kCgCheck; ++k) iteration(cs);
+            const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+            e = e2 != cudaSuccess ? e2 : cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    }
+    double h0[4] = {0.0, 0.0, 0.0, 0.0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h0, S, sizeof(h0), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     const double bnorm = sqrt(h0[3]);
     int it = 0;
     double rel = bnorm > 0.0 ? sqrt(h0[2]) / bnorm : 0.0;
     while (e == cudaSuccess && rel > tol && it < max_iter) {
-        const int upto = std::min(max_iter, it + kCgCheck);
-        for (; it < upto; ++it) {
-            k_cg_q<<<g, kFemThreads, 0, s>>>(n, F.rowptr, F.col, F.val, mask, p, q, S, it);
-            k_cg_update<<<g, kFemThreads, 0, s>>>(n, mask, F.diag, x, r, z, p, q, S, it);
-            k_cg_dir<<<g, kFemThreads, 0, s>>>(n, p, z, S, it);
+        if (max_iter - it >= kCgCheck) {
+            e = cudaGraphLaunch(exec, s);
+            it += kCgCheck;
+        } else {   // the last iterations below a whole replay
+            for (; it < max_iter; ++it) iteration(s);
+            e = cudaGetLastError();
         }
         double rr = 0.0;
-        e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(&rr, S + 4 * (size_t)it + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         rel = sqrt(rr) / bnorm;
     }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+    cudaStreamSynchronize(s);
     cudaFree(S);
+    cudaFree(cnt);
     if (e != cudaSuccess) {
         set_cuda_error(e, "conjugate gradients", __FILE__, __LINE__);
         return H2_ERR_CUDA;
