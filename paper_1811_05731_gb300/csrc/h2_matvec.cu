@@ -243,9 +243,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // (`packed`) each accumulator register pair holds a compensated FP32 sum
 // (hi word: sum, lo word: the TwoSum error terms), which the segment end
 // converts once; otherwise the chunk's sum is added to the FP64 accumulator.
-// With r == RT the inputs of one column are read as 16-byte vectors.  At
-// RT = 1 the FP64 products run in two chains, acc[0] and acc1, which persist
-// over the segment's chunks and meet at its end.
+// With r == RT the inputs of one column are read as 16-byte vectors, and the
+// FP32 products of two right-hand sides go through one packed FMA
+// (__ffma2_rn, each half rounded as fmaf): the FP32 far field at r = 16 is
+// bound by instruction issue, and the packed form halves its FMA
+// instructions.  At RT = 1 the FP64 products run in two chains, acc[0] and
+// acc1, which persist over the segment's chunks and meet at its end.
 template <int RT>
 __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const SPiece* pieces, int npieces,
                                               bool f32, const unsigned char* xin, int r, int nrows, int row,
@@ -291,9 +294,10 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const 
         }
         return;
     }
-    float acc32[RT];
+    // the chunk's FP32 sums, right-hand sides 2c and 2c + 1 in acc2[c]
+    float2 acc2[(RT + 1) / 2];
 #pragma unroll
-    for (int c = 0; c < RT; ++c) acc32[c] = 0.0f;
+    for (int c = 0; c < (RT + 1) / 2; ++c) acc2[c] = make_float2(0.0f, 0.0f);
     for (int p = 0; p < npieces; ++p) {
         const SPiece P = pieces[p];
         const int nc = P.ncols;
@@ -308,19 +312,18 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const 
                 a1 = fmaf(A[(col + G) * nrows], x[col + G], a1);
             }
             if (col < nc) a0 = fmaf(A[col * nrows], x[col], a0);
-            acc32[0] += a0 + a1;
+            acc2[0].x += a0 + a1;
         } else if (RT % 4 == 0 && r == RT) {   // 16-byte aligned rows of RT values
 #pragma unroll 2
             for (int col = g; col < nc; col += G) {
                 const float v = A[col * nrows];
+                const float2 v2 = make_float2(v, v);
                 const float4* x4 = reinterpret_cast<const float4*>(x + col * RT);
 #pragma unroll
                 for (int c = 0; c < RT / 4; ++c) {
                     const float4 xv = x4[c];
-                    acc32[4 * c] = fmaf(v, xv.x, acc32[4 * c]);
-                    acc32[4 * c + 1] = fmaf(v, xv.y, acc32[4 * c + 1]);
-                    acc32[4 * c + 2] = fmaf(v, xv.z, acc32[4 * c + 2]);
-                    acc32[4 * c + 3] = fmaf(v, xv.w, acc32[4 * c + 3]);
+                    acc2[2 * c] = __ffma2_rn(v2, make_float2(xv.x, xv.y), acc2[2 * c]);
+                    acc2[2 * c + 1] = __ffma2_rn(v2, make_float2(xv.z, xv.w), acc2[2 * c + 1]);
                 }
             }
         } else {
@@ -328,8 +331,11 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const 
             for (int col = g; col < nc; col += G) {
                 const float v = A[col * nrows];
 #pragma unroll
-                for (int c = 0; c < RT; ++c)
-                    if (c < r) acc32[c] = fmaf(v, x[col * r + c], acc32[c]);
+                for (int c = 0; c < RT; ++c) {
+                    if (c >= r) break;
+                    float& s = (c & 1) ? acc2[c >> 1].y : acc2[c >> 1].x;
+                    s = fmaf(v, x[col * r + c], s);
+                }
             }
         }
     }
@@ -337,13 +343,13 @@ __device__ __forceinline__ void consume_chunk(const unsigned char* stage, const 
 #pragma unroll
         for (int c = 0; c < RT; ++c) {
             float s, e;
-            two_sum(__int_as_float(__double2hiint(acc[c])), acc32[c], s, e);
+            two_sum(__int_as_float(__double2hiint(acc[c])), (c & 1) ? acc2[c >> 1].y : acc2[c >> 1].x, s, e);
             const float l = __int_as_float(__double2loint(acc[c])) + e;
             acc[c] = __hiloint2double(__float_as_int(s), __float_as_int(l));
         }
     } else {
 #pragma unroll
-        for (int c = 0; c < RT; ++c) acc[c] += (double)acc32[c];
+        for (int c = 0; c < RT; ++c) acc[c] += (double)((c & 1) ? acc2[c >> 1].y : acc2[c >> 1].x);
     }
 }
 
@@ -613,8 +619,13 @@ __host__ __device__ constexpr int red_rhs(int rt) { return rt <= 8 ? rt : 4; }
 // writer warps write the segment and, in the dataflow form, each signals the
 // segment's region with a release add.  No CTA-wide barrier is taken per
 // chunk and no wait is unbounded.
+// Registers: at r <= 16 (RT = 16, the split form's far-field launch) at most
+// 96 (104 with the tensor-core path), so that this CTA and a near-field CTA
+// at 64 registers share each SM sub-partition's 16 K registers even where
+// three warps of each meet (3 x 32 x 104 + 3 x 32 x 64 <= 16384); otherwise
+// as many as the 288 threads of one CTA per SM may take.
 template <int RT, bool FLOW, bool TC>
-__global__ void __launch_bounds__(kBlock, 1) k_seg(const KArgs a) {
+__global__ void __maxnreg__(RT == 16 ? (TC ? 104 : 96) : 168) k_seg(const KArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int S = a.stages;
     constexpr size_t kXin = xin_bytes(RT);
@@ -1185,24 +1196,50 @@ struct NStage {
 // beyond the unit's items issues no FP64 instruction for them: an FMA with
 // its lanes predicated off would still hold the FP64 pipe.
 // Item j of a thread is packed as row | (right-hand side << 8) (rows <= 64,
-// right-hand sides <= 16), so that the items fit the kernel's 40 registers.
+// right-hand sides <= 16).  The operands of column col + 1 are loaded before
+// the FMAs of column col issue: the FP64 pipe takes one warp FMA per 64
+// cycles per SM sub-partition, so a warp waits at its FMAs, and loads issued
+// behind them would leave the pipe idle for their latency whenever both of
+// the sub-partition's consumer warps reach a new column together.
 template <int NJ, int JM>
 __device__ __forceinline__ void near_item_cols(const double* __restrict__ A, const double* __restrict__ x, int nrows,
                                                int r, int ncols, const int (&item)[JM], double (&acc)[JM]) {
+    if (ncols <= 0) return;
+    int ao[NJ], xo[NJ];
+    double av[NJ], xv[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        ao[j] = item[j] & 0xFF;
+        xo[j] = item[j] >> 8;
+        av[j] = A[ao[j]];
+        xv[j] = x[xo[j]];
+    }
 #pragma unroll 1
-    for (int col = 0; col < ncols; ++col) {
+    for (int col = 1; col < ncols; ++col) {
         const double* Ac = A + col * nrows;
         const double* xc = x + col * r;
+        double an[NJ], xn[NJ];
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) acc[j] = fma(Ac[item[j] & 0xFF], xc[item[j] >> 8], acc[j]);
+        for (int j = 0; j < NJ; ++j) {
+            an[j] = Ac[ao[j]];
+            xn[j] = xc[xo[j]];
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            acc[j] = fma(av[j], xv[j], acc[j]);
+            av[j] = an[j];
+            xv[j] = xn[j];
+        }
     }
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[j] = fma(av[j], xv[j], acc[j]);
 }
 
-// At most 40 registers per thread: one CTA of this kernel and one of the
-// far-field launch at r <= 16 (288 threads x 128 registers) share each SM
-// sub-partition's 16 K registers even where three warps of each meet.
+// At most 64 registers per thread: one CTA of this kernel and one of the
+// far-field launch at r <= 16 (288 threads x at most 104 registers) share each
+// SM sub-partition's 16 K registers even where three warps of each meet.
 template <int RT, bool PAIR>
-__global__ void __maxnreg__(40) k_near_items(const NArgs a) {
+__global__ void __maxnreg__(64) k_near_items(const NArgs a) {
     constexpr int JM = RT / 4;   // items per thread: 64 rows x RT / 256 threads
     static_assert(!PAIR || JM >= 4, "paired form: four right-hand sides per thread");
     extern __shared__ __align__(128) unsigned char smem[];
