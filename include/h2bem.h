@@ -407,8 +407,11 @@ typedef struct {
  * one vector per tetrahedron).  u1, u2: DEVICE, n_vertices doubles each,
  * overwritten.  `op`: an operator on the boundary surface (its N = n_surf).
  * The solves stop at |r| <= tol |b| or after max_iter iterations each (see
- * the report).  Allocates scratch for the call; synchronous on
- * `cuda_stream`. */
+ * the report); the residual is checked every 8 iterations (they run as a
+ * CUDA graph captured on a stream of the library's own and launched on
+ * `cuda_stream`), so a solve may take up to 7 iterations past the one that
+ * met tol.  Allocates scratch for the call; synchronous on `cuda_stream`,
+ * which must not itself be capturing. */
 int h2_fem_solve(h2_handle* fem, h2_handle* op, const double* M, double* u1, double* u2, double tol,
                  int32_t max_iter, void* cuda_stream, h2_fem_report_t* out);
 
