@@ -144,6 +144,7 @@ struct KArgs {
     int r;                     // largest r of the launch's operators
     int stages;
     int stage_bytes;
+    int xin_bytes;             // input buffer of one stage (xin_bytes(RT); FP32 rows: xin_bytes_f32(RT))
     int tc;                    // the operator has tensor-core segments
     int tc_alo_bytes;          // shared memory for the TF32 lo parts of a chunk
     int tc_b_bytes;            // shared memory for the B operand (all its parts) of a chunk
@@ -588,6 +589,11 @@ __host__ __device__ constexpr int xin_cols(int rt) { return rt > 8 ? 64 : kMaxCh
 __host__ __device__ constexpr size_t xin_bytes(int rt) {
     return sizeof(double) * xin_cols(rt) * rt + 16 * H2_MAX_CHUNK_PIECES;
 }
+// The same for launches whose chunks all have FP32 inputs (the split form's
+// far field): half the bytes, which leaves room for another stage.
+__host__ __device__ constexpr size_t xin_bytes_f32(int rt) {
+    return sizeof(float) * xin_cols(rt) * rt + 16 * H2_MAX_CHUNK_PIECES;
+}
 
 // Partial-sum buffers of the segment kernel: two, alternating between the
 // reduction rounds of successive segments.
@@ -600,7 +606,8 @@ __host__ __device__ constexpr int red_rhs(int rt) { return rt <= 8 ? rt : 4; }
 
 // Shared-memory layout of the segment kernel (dynamic part):
 //   stages x stage_bytes             matrix chunks (bulk copies)
-//   stages x xin_bytes(RT)           the chunks' input values
+//   stages x a.xin_bytes             the chunks' input values (xin_bytes(RT), or
+//                                    xin_bytes_f32(RT) where no chunk has FP64 inputs)
 //   2 x kConsumers*red_rhs(RT)*8     partial sums of the row groups (two buffers)
 //   tc_sets x (tc_alo_bytes + tc_b_bytes)   tensor-core operands (TF32 lo parts of A,
 //                                    B with the rows of its vector parts)
@@ -628,11 +635,11 @@ template <int RT, bool FLOW, bool TC>
 __global__ void __maxnreg__(RT == 16 ? (TC ? 104 : 96) : 168) k_seg(const KArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int S = a.stages;
-    constexpr size_t kXin = xin_bytes(RT);
+    const size_t xin_sz = (size_t)a.xin_bytes;
     constexpr int RR = red_rhs(RT);
     unsigned char* stage_base = smem;
     unsigned char* xbase = smem + (size_t)S * a.stage_bytes;
-    double* red = reinterpret_cast<double*>(xbase + (size_t)S * kXin);
+    double* red = reinterpret_cast<double*>(xbase + (size_t)S * xin_sz);
     // tensor-core operands after the partial sums;
     // operand set q: [lo parts of A][B: hi rows, lo rows] at tc_base + q * tc_set_bytes
     unsigned char* tc_base = reinterpret_cast<unsigned char*>(red + kRedBuffers * kConsumers * RR);
@@ -763,8 +770,9 @@ __global__ void __maxnreg__(RT == 16 ? (TC ? 104 : 96) : 168) k_seg(const KArgs 
                 xoff -= mine;   // exclusive prefix
                 if (lane < cnp) spc[st][lane] = SPiece{pc.smem_off, pc.in_row, pc.ncols, xoff};
             }
-            bool ok = true;
-            if (FLOW && ci == 0 && lane == 0) ok = deps_wait(a, F, abortp);
+            // the chunk's inputs must fit the stage's input buffer (the host sizes it)
+            bool ok = in_total <= a.xin_bytes;
+            if (ok && FLOW && ci == 0 && lane == 0) ok = deps_wait(a, F, abortp);
             if (!__shfl_sync(~0u, ok, 0)) {
                 if (lane == 0) {
                     atomicExch(a.err, 1);
@@ -779,7 +787,7 @@ __global__ void __maxnreg__(RT == 16 ? (TC ? 104 : 96) : 168) k_seg(const KArgs 
                              "r"(in_total)
                              : "memory");
             __syncwarp();
-            issue_inputs(a.ctx[F.op], spc[st], cnp, f32, xbase + (size_t)st * kXin, &full[st], lane);
+            issue_inputs(a.ctx[F.op], spc[st], cnp, f32, xbase + (size_t)st * xin_sz, &full[st], lane);
             if (lane == 0) {
                 StageDesc D;
                 D.seg = sg;
@@ -832,7 +840,7 @@ __global__ void __maxnreg__(RT == 16 ? (TC ? 104 : 96) : 168) k_seg(const KArgs 
             if (TC && piece_tc(D.ptype) && !a.tc_cuda) {
                 // ---------- tensor-core chunk ----------
                 unsigned char* stg = stage_base + (size_t)st * a.stage_bytes;
-                const unsigned char* xin = xbase + (size_t)st * kXin;
+                const unsigned char* xin = xbase + (size_t)st * xin_sz;
                 const int type = D.ptype;
                 const int Mp = tc_rows(D.nrows);
                 const int Np = Mp == 64 ? (r + 7) / 8 * 8 : (r + 15) / 16 * 16;
@@ -1056,7 +1064,7 @@ __global__ void __maxnreg__(RT == 16 ? (TC ? 104 : 96) : 168) k_seg(const KArgs 
                     if (D.ptype == PIECE_NODES) {
                         const int t = (int)((D.out_row - C.row_yhat) / C.kp);
                         consume_nodes<RT>(stage_base + (size_t)st * a.stage_bytes, spc[st], D.npieces,
-                                          xbase + (size_t)st * kXin, r, C.nodes[(int64_t)t * C.kp + row], g, G,
+                                          xbase + (size_t)st * xin_sz, r, C.nodes[(int64_t)t * C.kp + row], g, G,
                                           acc);
                         done = true;
                     }
@@ -1064,13 +1072,13 @@ __global__ void __maxnreg__(RT == 16 ? (TC ? 104 : 96) : 168) k_seg(const KArgs 
                 if constexpr (!TC && RT <= kTcCudaMaxRT) {   // tensor tiles on the CUDA cores (a.tc_cuda)
                     if (!done && piece_tc(D.ptype)) {
                         consume_tc_tiles<RT>(stage_base + (size_t)st * a.stage_bytes, spc[st], D.npieces, D.ptype,
-                                             xbase + (size_t)st * kXin, r, nrows, row, g, G, acc);
+                                             xbase + (size_t)st * xin_sz, r, nrows, row, g, G, acc);
                         done = true;
                     }
                 }
                 if (!done)
                     consume_chunk<RT>(stage_base + (size_t)st * a.stage_bytes, spc[st], D.npieces, D.f32 != 0,
-                                      xbase + (size_t)st * kXin, r, nrows, row, g, G, D.out_f32 != 0, acc, acc1);
+                                      xbase + (size_t)st * xin_sz, r, nrows, row, g, G, D.out_f32 != 0, acc, acc1);
             }
             mbar_arrive(&empty[st]);
             if (D.last) {
@@ -1630,12 +1638,14 @@ static int tc_b_bytes(const h2_handle* op, int rt) {
 
 // Shared memory of the segment kernel with `sets` tensor-core operand sets of
 // `alo` + `b` bytes.
-static size_t seg_smem_raw(int rt, int stages, int stage_bytes, int alo, int b, int sets) {
+static size_t seg_smem_raw(int rt, int stages, int stage_bytes, int alo, int b, int sets,
+                           size_t xin = 0 /* 0: xin_bytes(rt) */) {
     const size_t S = (size_t)stages;
+    if (xin == 0) xin = xin_bytes(rt);
     const size_t red = (size_t)kRedBuffers * sizeof(double) * kConsumers * red_rhs(rt);
     const size_t tc = (size_t)sets * ((size_t)alo + (size_t)b);
     const size_t mid = red + tc;
-    return S * (size_t)stage_bytes + S * xin_bytes(rt) + mid + sizeof(uint64_t) * (2 * S + 5);
+    return S * (size_t)stage_bytes + S * xin + mid + sizeof(uint64_t) * (2 * S + 5);
 }
 
 // Shared-memory stages of the segment kernel for r <= rt right-hand sides.
@@ -1677,20 +1687,24 @@ static size_t near_smem_bytes(const h2_handle* op, int rt) {
 // far-field launch: three stages with one tensor-core operand set when both
 // launches still fit one SM's shared memory (static parts and reserve aside),
 // else two stages with two sets or one (measured: the third stage in flight
-// is worth more than the second set)
+// is worth more than the second set).  Its chunks all have FP32 inputs (the
+// near field is the other launch), so its input buffers hold FP32 rows,
+// which is what lets the BF16 hi + lo far field take the third stage.
 struct FarCfg {
     int stages, sets;
 };
 static FarCfg split_far_cfg(const h2_handle* op, int rt) {
     const size_t budget = (size_t)227 * 1024 - near_smem_bytes(op, rt) - (size_t)8 * 1024;
     const int alo = tc_alo_bytes(op), b = tc_b_bytes(op, rt);
-    if (seg_smem_raw(rt, 3, op->stage_bytes, alo, b, 1) <= budget) return FarCfg{3, 1};
-    if (seg_smem_raw(rt, 2, op->stage_bytes, alo, b, 2) <= budget) return FarCfg{2, 2};
+    const size_t xin = xin_bytes_f32(rt);   // no FP64 inputs without the near field
+    if (seg_smem_raw(rt, 3, op->stage_bytes, alo, b, 1, xin) <= budget) return FarCfg{3, 1};
+    if (seg_smem_raw(rt, 2, op->stage_bytes, alo, b, 2, xin) <= budget) return FarCfg{2, 2};
     return FarCfg{2, 1};
 }
 static size_t split_far_smem(const h2_handle* op, int rt) {
     const FarCfg c = split_far_cfg(op, rt);
-    return seg_smem_raw(rt, c.stages, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op, rt), c.sets);
+    return seg_smem_raw(rt, c.stages, op->stage_bytes, tc_alo_bytes(op), tc_b_bytes(op, rt), c.sets,
+                        xin_bytes_f32(rt));
 }
 
 // Profiling aid (h2_profile_enable): records a CUDA event before and after
@@ -1786,6 +1800,7 @@ static int launch_split(h2_handle* op, double* u2, int r, int rt, cudaStream_t s
     const FarCfg fc = split_far_cfg(op, rt);
     a.stages = fc.stages;
     a.stage_bytes = op->stage_bytes;
+    a.xin_bytes = (int)xin_bytes_f32(rt);
     a.tc = op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3;
     a.tc_alo_bytes = tc_alo_bytes(op);
     a.tc_b_bytes = tc_b_bytes(op, rt);
@@ -1875,6 +1890,7 @@ int launch_matvec(h2_handle* op, const double* u1, double* u2, int r, cudaStream
     a.r = r;
     a.stages = op_stages(op, rt);
     a.stage_bytes = op->stage_bytes;
+    a.xin_bytes = (int)xin_bytes(rt);
     a.tc = (op->params.precision == H2_TF32X3 || op->params.precision == H2_BF16X3) && !tc_cuda_for(op, rt);
     a.tc_alo_bytes = tc_alo_bytes(op);
     a.tc_b_bytes = tc_b_bytes(op, rt);
@@ -2503,6 +2519,7 @@ int matvec_batched(h2_handle* const* ops, int n, const double* const* u1, double
     a.r = rmax;
     a.stages = nst;
     a.stage_bytes = stage_bytes;
+    a.xin_bytes = (int)xin_bytes(rt);
     a.tc = tc && !tcc;
     a.tc_alo_bytes = alo;
     a.tc_b_bytes = b;
