@@ -1243,11 +1243,12 @@ __device__ __forceinline__ void near_item_cols(const double* __restrict__ A, con
     for (int j = 0; j < NJ; ++j) acc[j] = fma(av[j], xv[j], acc[j]);
 }
 
-// At most 64 registers per thread: one CTA of this kernel and one of the
-// far-field launch at r <= 16 (288 threads x at most 104 registers) share each
-// SM sub-partition's 16 K registers even where three warps of each meet.
+// At most 64 registers per thread (the paired form: 40, which it needs no
+// more than): one CTA of this kernel and one of the far-field launch at
+// r <= 16 (288 threads x at most 104 registers) share each SM sub-partition's
+// 16 K registers even where three warps of each meet.
 template <int RT, bool PAIR>
-__global__ void __maxnreg__(64) k_near_items(const NArgs a) {
+__global__ void __maxnreg__(PAIR ? 40 : 64) k_near_items(const NArgs a) {
     constexpr int JM = RT / 4;   // items per thread: 64 rows x RT / 256 threads
     static_assert(!PAIR || JM >= 4, "paired form: four right-hand sides per thread");
     extern __shared__ __align__(128) unsigned char smem[];
