@@ -1154,8 +1154,13 @@ __global__ void __maxnreg__(RT == 16 ? (TC ? 104 : 96) : 168) k_seg(const KArgs 
 // in FP64) and gives each thread one output row and four consecutive
 // right-hand sides instead, so that one entry load serves four products.
 // ---------------------------------------------------------------------------
-constexpr int kNearCons = 256;
-constexpr int kNearBlock = kNearCons + 32;
+// Consumer threads of the near-field kernel: twelve warps for the FP64 items
+// (three per SM sub-partition, so that two of them can wait on their operand
+// loads while the third keeps the FP64 pipe busy), eight for the paired form.
+template <bool PAIR>
+__host__ __device__ constexpr int near_cons() {
+    return PAIR ? 256 : 384;
+}
 
 // One term a*x of a paired near-field sum hi + lo (h2_near_field
 // H2_NEAR_F32PAIR; a, x = (hi, lo) FP32 pairs): the product of the high words
@@ -1243,13 +1248,17 @@ __device__ __forceinline__ void near_item_cols(const double* __restrict__ A, con
     for (int j = 0; j < NJ; ++j) acc[j] = fma(av[j], xv[j], acc[j]);
 }
 
-// At most 64 registers per thread (the paired form: 40, which it needs no
-// more than): one CTA of this kernel and one of the far-field launch at
-// r <= 16 (288 threads x at most 104 registers) share each SM sub-partition's
-// 16 K registers even where three warps of each meet.
+// At most 48 registers per thread (the paired form: 40): one CTA of this
+// kernel and one of the far-field launch at r <= 16 (288 threads x at most 104
+// registers) share each SM sub-partition's 16 K registers even where four
+// warps of this one meet three of the other (4 x 32 x 48 + 3 x 32 x 104 <=
+// 16384).
 template <int RT, bool PAIR>
-__global__ void __maxnreg__(PAIR ? 40 : 64) k_near_items(const NArgs a) {
-    constexpr int JM = RT / 4;   // items per thread: 64 rows x RT / 256 threads
+__global__ void __maxnreg__(PAIR ? 40 : 48) k_near_items(const NArgs a) {
+    constexpr int NC = near_cons<PAIR>();
+    // items per thread: 64 rows x RT over the NC threads (paired: four
+    // right-hand sides of one row)
+    constexpr int JM = PAIR ? RT / 4 : (64 * RT + NC - 1) / NC;
     static_assert(!PAIR || JM >= 4, "paired form: four right-hand sides per thread");
     extern __shared__ __align__(128) unsigned char smem[];
     const int S = a.stages;
@@ -1266,7 +1275,7 @@ __global__ void __maxnreg__(PAIR ? 40 : 64) k_near_items(const NArgs a) {
         abort_flag = 0;
         for (int q = 0; q < S; ++q) {
             mbar_init(&full[q], 2);
-            mbar_init(&empty[q], kNearCons);
+            mbar_init(&empty[q], NC);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -1274,7 +1283,7 @@ __global__ void __maxnreg__(PAIR ? 40 : 64) k_near_items(const NArgs a) {
     volatile int* abortp = &abort_flag;
     int issued = 0;
     const int r = a.r;
-    if (tid >= kNearCons) {
+    if (tid >= NC) {
         // ---------------- producer warp ----------------
         const int lane = tid & 31;
         int i = 0;
@@ -1387,9 +1396,9 @@ __global__ void __maxnreg__(PAIR ? 40 : 64) k_near_items(const NArgs a) {
                     nj = 0;
 #pragma unroll
                     for (int j = 0; j < JM; ++j) {
-                        const int it = tid + kNearCons * j;
+                        const int it = tid + NC * j;
                         item[j] = it < nitems ? (it % nrows) | ((it / nrows) << 8) : 0;
-                        if ((tid & ~31) + kNearCons * j < nitems) nj = j + 1;
+                        if ((tid & ~31) + NC * j < nitems) nj = j + 1;
                     }
                 }
             }
@@ -1422,9 +1431,8 @@ __global__ void __maxnreg__(PAIR ? 40 : 64) k_near_items(const NArgs a) {
                 } else {
                     const double* A = reinterpret_cast<const double*>(stg + P.smem_off);
                     const double* x = reinterpret_cast<const double*>(xin + P.xoff);
-                    static_assert(JM == 4, "the FP64 item form is instantiated for 16 right-hand sides");
+                    static_assert(JM == 3, "the FP64 item form is instantiated for 16 right-hand sides");
                     switch (nj) {   // warp-uniform
-                        case 4: near_item_cols<4>(A, x, nrows, r, P.ncols, item, acc); break;
                         case 3: near_item_cols<3>(A, x, nrows, r, P.ncols, item, acc); break;
                         case 2: near_item_cols<2>(A, x, nrows, r, P.ncols, item, acc); break;
                         case 1: near_item_cols<1>(A, x, nrows, r, P.ncols, item, acc); break;
@@ -1441,7 +1449,7 @@ __global__ void __maxnreg__(PAIR ? 40 : 64) k_near_items(const NArgs a) {
                             atomicAdd(a.u2n + (int64_t)(prhs0 + j) * a.N + a.perm[D.out_row + prow],
                                       (double)hi[j] + (double)lo[j]);
                     } else {
-                        if (tid + kNearCons * j < nitems)
+                        if (tid + NC * j < nitems)
                             atomicAdd(a.u2n + (int64_t)(item[j] >> 8) * a.N + a.perm[D.out_row + (item[j] & 0xFF)],
                                       acc[j]);
                     }
@@ -1454,7 +1462,7 @@ __global__ void __maxnreg__(PAIR ? 40 : 64) k_near_items(const NArgs a) {
     }
     __syncthreads();
     // after an abort, let the producer's copies still in flight land (bounded)
-    if (tid == kNearCons && abort_flag) {
+    if (tid == NC && abort_flag) {
         for (int j = issued > S ? issued - S : 0; j < issued; ++j)
             (void)mbar_wait(&full[j % S], (uint32_t)(j / S) & 1u);
     }
@@ -1750,7 +1758,7 @@ template <int RT, bool PAIR>
 cudaError_t launch_near_rt(const NArgs& a, int nsm, size_t smem, cudaStream_t s) {
     cudaError_t e = set_smem(k_near_items<RT, PAIR>, smem);
     if (e != cudaSuccess) return e;
-    k_near_items<RT, PAIR><<<nsm, kNearBlock, smem, s>>>(a);
+    k_near_items<RT, PAIR><<<nsm, near_cons<PAIR>() + 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
