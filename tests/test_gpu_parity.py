@@ -340,6 +340,32 @@ def test_paired_near_field_all_near_operator_is_the_dense_matrix():
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("leaf", [7, 16, 33, 64])
+def test_split_near_field_all_near_operator_is_the_dense_matrix(precision, leaf):
+    """eta -> 0 leaves only exact near blocks, so a reduced-precision
+    operator's split-form product is the FP64 near-field kernel alone: it
+    must match x M^T to 1e-12.  The leaf sizes give units of a few to 64 rows
+    (one to three item slots per thread, warps whose last slot is partly
+    filled), and r = 16, 13, 9 leaves right-hand sides past r in the items'
+    range; three calls cover the direct launch, the graph capture and its
+    replay."""
+    m = synth.icosphere(3)
+    g = pkg.Geometry(m.xyz, m.tri)
+    M = oracle.dense_matrix(m.xyz, m.tri)
+    op = pkg.Operator(g, m=3, leaf=leaf, eta=1e-9, max_rhs=16, precision=PRECISIONS[precision])
+    assert op.stats()["n_far_blocks"] == 0
+    assert op.stats()["n_launches_matvec"] == 4   # the split form
+    for r in (16, 13, 9):
+        x = np.vstack([synth.gaussian_rhs(m.n_vertices, r - 1, 5 + r), np.ones((1, m.n_vertices))])
+        xt = torch.from_numpy(x).cuda()
+        for _ in range(3 if r == 16 else 1):
+            y = op.matvec(xt, nan_out(xt)).cpu().numpy()
+            assert pkg.h2_device_status(op.handle) == 0
+            assert np.max(np.abs(y - x @ M.T)) < 1e-12, (leaf, r)
+            assert np.max(np.abs(y[-1] + 1.0)) < 1e-12   # Gauss: M 1 = -1
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 def test_paired_near_field_within_budget(precision):
     """The paired near field in the split form with a far field: the product
     meets the budget against the oracle for r at and below the operator's
